@@ -1,0 +1,295 @@
+"""Benchmark: INLA f + grad evaluations per second on one GB300.
+
+Workload: univariate spatio-temporal model on a 32x32 grid (b = 1024),
+n_t = 50 time blocks, a = 6 fixed effects, d = 4, 1e5 observations
+(seeded synthetic data).  One step = one call of inla_value_and_grad (all
+of the hot path: assembly of Q_p and Q_c, both BTA factorisations, the
+solve for x*, f, both in-place selected inversions with the fused Phase A/C
+traces, Phase B and the explicit terms).  The working set (two factors of
+0.84 GB each) is far larger than L2, so no flush is needed between steps.
+
+Also reported: the 2d+1 central finite-difference gradient (value-only
+evaluations) on the same GPU, the FP64 efficiency of the whole step, the
+roofline of the dominant kernel (the FP64 tile GEMM at the sweep's block
+shape, timed live), and the FP64 CPU oracle on a bounded sample.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "INLA f+∇f evals/s on 1 GB300: AD vs 2d+1 FD; % FP64 TC peak; rel err vs FP64"
+UNIT = "gradient evaluations/s"
+WORKLOAD = "st_medium"
+# FP64 peak of the arithmetic unit the path uses (DFMA, "alu"): 152 SMs x 2 FP64
+# FMA/clock/SM x 2 flop x 2.07 GHz maximum SM clock.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def _flops_model(b, n, a):
+    """Algorithmic FP64 flops of one f+grad and of one value-only evaluation
+    with the block kernels as implemented (per matrix and block: factor
+    8/3 b^3 = SYRK b^3 + POTRF b^3/3 + TRTRI b^3/3 + TRMM b^3; selected
+    inversion 13/3 b^3), arrow terms O(a b^2) included."""
+    b3 = float(b) ** 3
+    fwd = 2 * n * (8.0 / 3.0) * b3 + n * (4 * a * b * b)
+    bwd = 2 * n * (13.0 / 3.0) * b3 + n * (6 * a * b * b)
+    return fwd + bwd, fwd
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self):
+        self.rows = []
+        self._stop = threading.Event()
+        self._proc = None
+
+    def start(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            idx = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or "0"
+            self._proc = subprocess.Popen(
+                ["nvidia-smi", "-i", idx, f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except Exception:
+            self._proc = None
+
+    def _read(self):
+        for line in self._proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self._proc:
+            self._proc.terminate()
+            try:
+                self._proc.wait(timeout=5)
+            except Exception:
+                self._proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for i, nm in enumerate(names):
+                if len(r) > 4 + i and r[4 + i].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.rows)}
+
+
+def cpu_baseline(seconds_hint: float = 20.0):
+    """The FP64 oracle's block sweep (f and gradient) on a bounded sample of
+    the workload: the same 32x32-grid model with 6 of its 50 time blocks;
+    the per-block cost is constant, so the full-size time is the sample's
+    time x 50/6."""
+    import workloads
+    from oracle import bta
+    prob = workloads.make_problem("st_medium_nt6")
+    t0 = time.perf_counter()
+    bta.evaluate(prob)
+    dt = time.perf_counter() - t0
+    full = workloads.WORKLOADS[WORKLOAD]["nt"]
+    t_full = dt * full / prob.nt
+    return {"value": 1.0 / t_full, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"oracle f+grad on the {WORKLOAD} model cut to nt={prob.nt} of {full} "
+                      f"time blocks ({dt:.1f} s), scaled by {full}/{prob.nt}",
+            "seconds_per_gradient": t_full}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    times = []
+    cb = None
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline()
+        if i >= args.warmup:
+            times.append(cb["seconds_per_gradient"])
+    t = float(np.mean(times))
+    line = {"impl": "reference", "metric": METRIC, "value": 1.0 / t, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": "32x32", "b": 1024, "nt": 50, "a": 6,
+                       "d": 4, "n_obs": 100000},
+            "cpu_baseline": {"value": 1.0 / t, "unit": UNIT, "cores": cb["cores"],
+                             "kind": "oracle", "sample": cb["sample"]},
+            "e2e": {"value": 1.0 / t, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def gemm_roofline(P, torch, b, reps=5):
+    """Average duration of the FP64 tile GEMM at the sweep's dense block
+    shape (b x b x b, the Z_B = -Z_D,i+1 F_B product of the selected
+    inversion), timed with CUDA events on its launch stream."""
+    A = torch.randn(b, b, dtype=torch.float64, device="cuda")
+    B = torch.randn(b, b, dtype=torch.float64, device="cuda")
+    Cm = torch.zeros(b, b, dtype=torch.float64, device="cuda")
+    s = torch.cuda.current_stream()
+    for _ in range(2):
+        P.bta_gemm(A, B, Cm, stream=s)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(s)
+    for _ in range(reps):
+        P.bta_gemm(A, B, Cm, stream=s)
+    e1.record(s)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    flops = 2.0 * b ** 3
+    return ms, flops / (ms * 1e-3) / 1e12
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fd-steps", type=int, default=2)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2605_06392_gb300 as P
+    import workloads
+
+    prob = workloads.make_problem(WORKLOAD)
+    model = P.InlaModel(prob)
+    theta = prob.theta.copy()
+    stream = torch.cuda.current_stream()
+    # warm-up (also captures the CUDA graphs)
+    for _ in range(args.warmup):
+        f, g = model.value_and_grad(theta)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # --- timed region: K gradient evaluations, device time by CUDA events
+    clocks = ClockSampler()
+    clocks.start()
+    barrier()
+    k0 = model.kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    host_times = []
+    e0.record(stream)
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        f, g = model.value_and_grad(theta)          # host theta in, host f/grad out
+        host_times.append(time.perf_counter() - t0)
+    e1.record(stream)
+    e1.synchronize()
+    barrier()
+    clocks.stop()
+    launches = model.kernel_launches() - k0
+    ms = e0.elapsed_time(e1) / args.steps
+    t_step = ms * 1e-3
+    if dist is not None:
+        tt = torch.tensor([t_step, float(np.mean(host_times))], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step, t_host = float(tt[0]), float(tt[1])
+    else:
+        t_host = float(np.mean(host_times))
+    value = world / t_step
+    e2e = world / t_host
+
+    # --- FD baseline: 2d+1 value-only evaluations per gradient, same GPU
+    pts = workloads.fd_stencil(theta, 1e-3)
+    model.value_and_grad(pts[:2], grad=False)       # warm the value-only graph
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.fd_steps):
+        fv, _ = model.value_and_grad(pts, grad=False)
+    t_fd = (time.perf_counter() - t0) / args.fd_steps
+    g_fd = (fv[1::2] - fv[2::2]) / 2e-3
+
+    # --- dominant kernel roofline
+    gemm_ms, gemm_tf = gemm_roofline(P, torch, prob.b)
+
+    parts = model.last_parts()
+    flops_grad, flops_val = _flops_model(prob.b, prob.nt, prob.a)
+    step_tf = flops_grad / t_step / 1e12
+    out = None
+    if rank == 0:
+        cpu = None if args.no_cpu else cpu_baseline()
+        if cpu is not None:
+            cpu.pop("seconds_per_gradient", None)
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": "32x32", "b": prob.b, "ld": model.ld,
+                       "nt": prob.nt, "a": prob.a, "d": prob.d, "n_obs": prob.n_obs,
+                       "l2": "working set 1.7 GB > L2, no flush", "parallelism": "replicas"},
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 8 * prob.d,
+                    "d2h_bytes_per_step": 8 * (1 + prob.d + 8 + 4 * prob.d)},
+            "gpu_launches": int(launches),
+            "fd_baseline": {"seconds_per_gradient": t_fd, "evals_per_gradient": pts.shape[0],
+                            "gradients_per_s": 1.0 / t_fd,
+                            "speedup_ad_vs_fd": t_fd / t_step,
+                            "c_ad": t_step / (t_fd / pts.shape[0]),
+                            "max_rel_diff_fd_vs_ad": float(np.max(np.abs(g_fd - g) /
+                                                                  np.maximum(np.abs(g), 1.0)))},
+            "fp64_step": {"algorithmic_tflop_per_step": flops_grad / 1e12,
+                          "achieved_tflops": step_tf, "frac_of_peak": step_tf / FP64_PEAK_TFLOPS},
+            "roofline": {"bound": "alu", "kernel": "gemm_f64_kernel<64,64> (b x b x b)",
+                         "achieved": gemm_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": gemm_tf / FP64_PEAK_TFLOPS, "traffic": None,
+                         "launch_ms": gemm_ms,
+                         "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz"},
+            "clocks": clocks.summary(),
+            "result": {"f": f, "grad": [float(v) for v in g], "logdet_c": parts["logdet_c"],
+                       "logdet_p": parts["logdet_p"]},
+        }
+        if cpu is not None:
+            out["cpu_baseline"] = cpu
+        print(json.dumps(out), flush=True)
+    model.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

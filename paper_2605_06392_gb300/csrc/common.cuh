@@ -1,0 +1,102 @@
+// Shared definitions for the BTA / INLA CUDA library (sm_103a, FP64 path).
+#pragma once
+
+#include <cstdint>
+#include <cstdio>
+#include <cuda_runtime.h>
+
+#include "../../include/bta.h"
+
+namespace bta {
+
+// All block sizes are padded to a multiple of this tile (the padding holds the
+// identity on diagonal blocks and zeros elsewhere).
+constexpr int kPad = 32;
+
+// Number of kernels launched by this library (process-wide and per model).
+extern int64_t g_launches;
+
+#define BTA_CUDA_TRY(expr)                                                    \
+  do {                                                                        \
+    cudaError_t _e = (expr);                                                  \
+    if (_e != cudaSuccess) {                                                  \
+      fprintf(stderr, "[bta] %s failed: %s (%s:%d)\n", #expr,                 \
+              cudaGetErrorString(_e), __FILE__, __LINE__);                    \
+      return _e == cudaErrorMemoryAllocation ? BTA_ERR_NOMEM : BTA_ERR_CUDA;  \
+    }                                                                         \
+  } while (0)
+
+#define BTA_TRY(expr)                                                         \
+  do {                                                                        \
+    bta_status _s = (expr);                                                   \
+    if (_s != BTA_OK) return _s;                                              \
+  } while (0)
+
+// After a kernel launch: count it and surface launch-configuration errors.
+#define BTA_LAUNCHED()                                                        \
+  do {                                                                        \
+    ++::bta::g_launches;                                                      \
+    cudaError_t _e = cudaPeekAtLastError();                                   \
+    if (_e != cudaSuccess) {                                                  \
+      fprintf(stderr, "[bta] launch failed: %s (%s:%d)\n",                    \
+              cudaGetErrorString(_e), __FILE__, __LINE__);                    \
+      return BTA_ERR_CUDA;                                                    \
+    }                                                                         \
+  } while (0)
+
+inline int pad_ld(int b) { return (b + kPad - 1) / kPad * kPad; }
+inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// ----------------------------------------------------------------------------
+// Dense FP64 tile GEMM (gemm_f64.cu)
+// C[M x N] = alpha * op(A) * op(B) + beta * Cin, column-major.
+// tri flags mask the operand outside its triangle (the stored values there
+// are ignored) and skip the all-zero K ranges.
+// ----------------------------------------------------------------------------
+enum Tri : int { TRI_NONE = 0, TRI_LOWER = 1, TRI_UPPER = 2 };
+
+struct Gemm {
+  int M = 0, N = 0, K = 0;
+  const double* A = nullptr; int lda = 0; int transA = 0; int triA = TRI_NONE;
+  const double* B = nullptr; int ldb = 0; int transB = 0; int triB = TRI_NONE;
+  double* C = nullptr; int ldc = 0;
+  const double* Cin = nullptr; int ldcin = 0;   // may alias C; ignored when beta == 0
+  double alpha = 1.0, beta = 0.0;
+  int out_lower = 0;   // write only C[i][j] with i >= j (tiles above the diagonal skipped)
+  // batched: blockIdx.z selects problem z, pointers advance by these strides
+  int batch = 1;
+  int64_t strideA = 0, strideB = 0, strideC = 0, strideCin = 0;
+};
+bta_status gemm_f64(const Gemm& g, cudaStream_t s);
+
+// y[M] = alpha * op(A) x + beta * yin ; A column-major lda; tri masks A.
+struct Gemv {
+  int M = 0, K = 0;
+  const double* A = nullptr; int lda = 0; int transA = 0; int triA = TRI_NONE;
+  const double* x = nullptr;
+  double* y = nullptr;
+  const double* yin = nullptr;    // may alias y
+  double alpha = 1.0, beta = 0.0;
+};
+bta_status gemv_f64(const Gemv& g, double* work, cudaStream_t s);
+constexpr int kGemvSplit = 16;      // K splits; work needs kGemvSplit * M doubles
+
+// ----------------------------------------------------------------------------
+// Diagonal-block Cholesky + inverse (potrf.cu)
+// On return the lower triangle of A (n x n, ld) holds L^{-1} where A = L L^T;
+// logdet_parts[slot0 + j] receives 2 sum log diag over base tile j;
+// *fail receives `fail_code` if a pivot was not positive.
+// scratch: at least n*n doubles.
+// ----------------------------------------------------------------------------
+bta_status potrf_inv(double* A, int n, int ld, double* scratch, double* logdet_parts,
+                     int32_t* fail, int32_t fail_code, cudaStream_t s);
+int potrf_inv_slots(int n);   // number of logdet slots potrf_inv writes
+
+// Small helpers (sweep.cu)
+bta_status copy_block(const double* src, int lds, double* dst, int ldd, int rows, int cols,
+                      double alpha, int mode, cudaStream_t s);  // mode 0 copy, 1 mirror lower->full
+bta_status fill_value(double* p, int64_t n, double v, cudaStream_t s);
+bta_status sum_slots(const double* parts, int nparts, double* out, int accumulate,
+                     cudaStream_t s);
+
+}  // namespace bta

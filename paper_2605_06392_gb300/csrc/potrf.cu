@@ -1,0 +1,140 @@
+// Cholesky factor and its inverse for one dense SPD diagonal block (FP64).
+//
+// The BTA sweeps use L_Di only through L_Di^{-1}: the off-diagonal factors
+// L_Bi = B_i L_Di^{-T} and L_Ci, the lower and upper solves (Algorithm 1,
+// Eqs. 3-5) and the selected inversion all become products with L_Di^{-1},
+// which parallelise over every output tile instead of running as
+// column-sequential triangular solves.  This routine therefore overwrites
+// the lower triangle of A with L^{-1} (A = L L^T) and records log|A|.
+//
+// Recursive formulation on a 2 x 2 split (n1 + n2), all big steps being
+// tile-parallel products:
+//     [A11      ]   L11 = chol(A11),         W = L11^{-1} (recursive)
+//     [A21  A22 ]   L21 = A21 L11^{-T}
+//                   A22 <- A22 - L21 L21^T,  L22^{-1} (recursive)
+//                   (L^{-1})21 = -L22^{-1} L21 L11^{-1}
+// with a single-CTA shared-memory kernel for 32 x 32 leaves.
+#include <cmath>
+
+#include "common.cuh"
+
+namespace bta {
+namespace {
+
+constexpr int T = kPad;   // leaf size
+
+__global__ void __launch_bounds__(256) potrf_inv_leaf(double* A, int ld, double* logdet_slot,
+                                                      int32_t* fail, int32_t fail_code) {
+  __shared__ double L[T][T + 1];
+  __shared__ double W[T][T + 1];
+  __shared__ int bad;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < T * T; e += blockDim.x) {
+    int i = e % T, j = e / T;
+    L[i][j] = (i >= j) ? A[i + (int64_t)j * ld] : 0.0;
+  }
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  // Right-looking Cholesky of the leaf.
+  for (int j = 0; j < T; ++j) {
+    if (tid == 0) {
+      double d = L[j][j];
+      if (!(d > 0.0) || !isfinite(d)) { bad = 1; d = 1.0; }
+      L[j][j] = sqrt(d);
+    }
+    __syncthreads();
+    double piv = L[j][j];
+    for (int i = j + 1 + tid; i < T; i += blockDim.x) L[i][j] /= piv;
+    __syncthreads();
+    // trailing update of the lower triangle, columns j+1..T-1
+    int rem = T - j - 1;
+    for (int e = tid; e < rem * rem; e += blockDim.x) {
+      int i = j + 1 + e % rem, k = j + 1 + e / rem;
+      if (i >= k) L[i][k] = fma(-L[i][j], L[k][j], L[i][k]);
+    }
+    __syncthreads();
+  }
+  // Inverse of the lower-triangular leaf: thread c forms column c.
+  if (tid < T) {
+    int c = tid;
+    for (int i = 0; i < c; ++i) W[i][c] = 0.0;
+    W[c][c] = 1.0 / L[c][c];
+    for (int i = c + 1; i < T; ++i) {
+      double s = 0.0;
+      for (int k = c; k < i; ++k) s = fma(L[i][k], W[k][c], s);
+      W[i][c] = -s / L[i][i];
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < T * T; e += blockDim.x) {
+    int i = e % T, j = e / T;
+    if (i >= j) A[i + (int64_t)j * ld] = W[i][j];
+  }
+  if (tid == 0) {
+    double s = 0.0;
+    for (int j = 0; j < T; ++j) s += log(L[j][j]);
+    *logdet_slot = 2.0 * s;
+    if (bad) atomicCAS(fail, -1, fail_code);
+  }
+}
+
+bta_status rec(double* A, int n, int ld, double* scratch, double* slots, int32_t* fail,
+               int32_t fail_code, cudaStream_t s) {
+  if (n == T) {
+    potrf_inv_leaf<<<1, 256, 0, s>>>(A, ld, slots, fail, fail_code);
+    BTA_LAUNCHED();
+    return BTA_OK;
+  }
+  int p = n / T;
+  int n1 = (p / 2) * T, n2 = n - n1;
+  double* A11 = A;
+  double* A21 = A + n1;
+  double* A22 = A + n1 + (int64_t)n1 * ld;
+  double* W1 = scratch;                       // n2 x n1, ld n2 : L21
+  double* W2 = scratch + (int64_t)n2 * n1;    // n2 x n1        : L21 L11^{-1}
+  double* sub = W2 + (int64_t)n2 * n1;        // scratch for the recursion on A22
+  BTA_TRY(rec(A11, n1, ld, sub, slots, fail, fail_code, s));
+  {  // L21 = A21 * (L11^{-1})^T
+    Gemm g; g.M = n2; g.N = n1; g.K = n1;
+    g.A = A21; g.lda = ld;
+    g.B = A11; g.ldb = ld; g.transB = 1; g.triB = TRI_UPPER;   // (lower W)^T is upper
+    g.C = W1; g.ldc = n2;
+    BTA_TRY(gemm_f64(g, s));
+  }
+  {  // A22 -= L21 L21^T (lower)
+    Gemm g; g.M = n2; g.N = n2; g.K = n1;
+    g.A = W1; g.lda = n2;
+    g.B = W1; g.ldb = n2; g.transB = 1;
+    g.C = A22; g.ldc = ld; g.Cin = A22; g.ldcin = ld;
+    g.alpha = -1.0; g.beta = 1.0; g.out_lower = 1;
+    BTA_TRY(gemm_f64(g, s));
+  }
+  BTA_TRY(rec(A22, n2, ld, sub, slots + n1 / T, fail, fail_code, s));
+  {  // W2 = L21 * L11^{-1}
+    Gemm g; g.M = n2; g.N = n1; g.K = n1;
+    g.A = W1; g.lda = n2;
+    g.B = A11; g.ldb = ld; g.triB = TRI_LOWER;
+    g.C = W2; g.ldc = n2;
+    BTA_TRY(gemm_f64(g, s));
+  }
+  {  // (L^{-1})21 = -L22^{-1} W2
+    Gemm g; g.M = n2; g.N = n1; g.K = n2;
+    g.A = A22; g.lda = ld; g.triA = TRI_LOWER;
+    g.B = W2; g.ldb = n2;
+    g.C = A21; g.ldc = ld; g.alpha = -1.0;
+    BTA_TRY(gemm_f64(g, s));
+  }
+  return BTA_OK;
+}
+
+}  // namespace
+
+int potrf_inv_slots(int n) { return n / T; }
+
+bta_status potrf_inv(double* A, int n, int ld, double* scratch, double* logdet_parts,
+                     int32_t* fail, int32_t fail_code, cudaStream_t s) {
+  if (n <= 0 || n % T) return BTA_ERR_ARG;
+  return rec(A, n, ld, scratch, logdet_parts, fail, fail_code, s);
+}
+
+}  // namespace bta

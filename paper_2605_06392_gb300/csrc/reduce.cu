@@ -1,0 +1,305 @@
+// Reductions of the gradient phases (Eq. 6) and of f (Eq. 1).
+//
+//  * Phase A / C (Eq. 7): every block Jacobian is a combination of the few
+//    base stencils, dD_t/dth_k = sum_{pq,s} d alpha^D_{t,pq,s} S_s (plus the
+//    count diagonal and the arrow for log tau), so tr(Z_D dD) reduces to the
+//    stencil inner products <Z_D^(pq), S_s>, read only on the stencil
+//    pattern (O(nnz) per block, independent of d).
+//  * Phase B (Eq. 8): the same expansion turns x^T dQ_p x into stencil
+//    quadratic forms x_t^(p)T S_s x_u^(q).
+//  * log l: squared residuals y - A x* per response.
+// All partial sums are written to fixed slots and summed in a fixed order,
+// so results are bit-reproducible run to run.
+#include <algorithm>
+#include <cmath>
+
+#include "model.cuh"
+
+namespace bta {
+namespace {
+
+constexpr int RT = 256;
+
+template <int NV>
+__device__ void block_sum(double (&v)[NV], double* out, int stride) {
+  __shared__ double sh[NV][RT / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    double x = v[i];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if (lane == 0) sh[i][w] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double s = 0.0;
+    for (int j = 0; j < RT / 32; ++j) s += sh[threadIdx.x][j];
+    out[threadIdx.x * stride] = s;
+  }
+}
+
+struct PatArgs {
+  int k, ns, ld, nnz;
+  const int32_t* row_of;
+  const int32_t* col;
+  const double* val;
+  const double* cnt;   // [ld] of this block, or null
+};
+
+// out[((pq * chunks) + chunk) * kNP + s]
+__global__ void __launch_bounds__(RT) pattern_dot_kernel(PatArgs a, const double* __restrict__ Z,
+                                                         double* out) {
+  const int chunk = blockIdx.x, pq = blockIdx.y;
+  const int p = pq / a.k, q = pq % a.k;
+  const int e = chunk * RT + threadIdx.x;
+  double v[kNP] = {0.0, 0.0, 0.0, 0.0};
+  if (e < a.nnz) {
+    int s2 = a.row_of[e], s1 = a.col[e];
+    int r = p * a.ns + s1, c = q * a.ns + s2;
+    double z = Z[r + (int64_t)c * a.ld];
+    v[0] = z * a.val[e];
+    v[1] = z * a.val[a.nnz + e];
+    v[2] = z * a.val[2 * a.nnz + e];
+    if (a.cnt && p == q && s1 == s2) v[3] = z * a.cnt[r];
+  }
+  block_sum<kNP>(v, out + ((int64_t)pq * gridDim.x + chunk) * kNP, 1);
+}
+
+__global__ void __launch_bounds__(RT) pattern_quad_kernel(PatArgs a, const double* __restrict__ xr,
+                                                          const double* __restrict__ xc,
+                                                          double* out) {
+  const int chunk = blockIdx.x, pq = blockIdx.y;
+  const int p = pq / a.k, q = pq % a.k;
+  const int e = chunk * RT + threadIdx.x;
+  double v[kNP] = {0.0, 0.0, 0.0, 0.0};
+  if (e < a.nnz) {
+    int s2 = a.row_of[e], s1 = a.col[e];
+    double z = xr[p * a.ns + s1] * xc[q * a.ns + s2];
+    v[0] = z * a.val[e];
+    v[1] = z * a.val[a.nnz + e];
+    v[2] = z * a.val[2 * a.nnz + e];
+  }
+  block_sum<kNP>(v, out + ((int64_t)pq * gridDim.x + chunk) * kNP, 1);
+}
+
+// <Z_C, craw> restricted to variable m: rows m*a_r.., columns m*ns..
+__global__ void __launch_bounds__(RT) arrow_dot_kernel(int ns, int a, int a_r,
+                                                       const double* __restrict__ ZC,
+                                                       const double* __restrict__ craw,
+                                                       double* out) {
+  const int chunk = blockIdx.x, m = blockIdx.y;
+  const int i = chunk * RT + threadIdx.x;
+  double v[1] = {0.0};
+  if (i < a_r * ns) {
+    int f = m * a_r + i % a_r;
+    int c = m * ns + i / a_r;
+    int64_t idx = f + (int64_t)c * a;
+    v[0] = ZC[idx] * craw[idx];
+  }
+  block_sum<1>(v, out + (int64_t)m * gridDim.x + chunk, 1);
+}
+
+__global__ void __launch_bounds__(RT) residual_kernel(int64_t n_obs, int per, int k, int a_r,
+                                                      int64_t fe0, const int32_t* __restrict__ lat,
+                                                      const int32_t* __restrict__ var,
+                                                      const double* __restrict__ cov,
+                                                      const double* __restrict__ y,
+                                                      const double* __restrict__ x, double* out) {
+  double v[kMaxK] = {0.0, 0.0, 0.0, 0.0};
+  int64_t beg = (int64_t)blockIdx.x * per, end = min(n_obs, beg + per);
+  for (int64_t j = beg + threadIdx.x; j < end; j += RT) {
+    int m = var[j];
+    double r = y[j] - x[lat[j]];
+    const double* cj = cov + j * a_r;
+    const double* beta = x + fe0 + (int64_t)m * a_r;
+    for (int c = 0; c < a_r; ++c) r -= cj[c] * beta[c];
+#pragma unroll
+    for (int mm = 0; mm < kMaxK; ++mm)
+      if (mm == m) v[mm] = fma(r, r, v[mm]);
+  }
+  block_sum<kMaxK>(v, out + blockIdx.x, gridDim.x);
+}
+
+struct FinArgs {
+  int k, d, nt, a, a_r, ld, kk, pch, ach, rch, nldc, nldp, grad;
+  double tip, pvar;
+  const double* m_diag;
+  const double* m_sub;
+  const double* traw;
+  double n_var[kMaxK];
+  CoefLayout L;
+  Reductions r;
+};
+
+__global__ void __launch_bounds__(RT) finalize_kernel(FinArgs a, const double* coefbuf,
+                                                      double* out) {
+  // R[j][pq][s] sums for Q_c (RDc), Q_p (RDp) and the mode's quadratic form (RX).
+  __shared__ double RDc[kNJ][kMaxK * kMaxK][kNS], RDp[kNJ][kMaxK * kMaxK][kNS],
+      RX[kNJ][kMaxK * kMaxK][kNS];
+  __shared__ double CNT[kMaxK], PC[kMaxK], TT[kMaxK], RS[kMaxK];
+  const int tid = threadIdx.x, kk = a.kk, nt = a.nt, pch = a.pch;
+  const Reductions& r = a.r;
+  // thread -> (which of 3 arrays, pq, s)
+  for (int w = tid; w < 3 * kk * kNS; w += blockDim.x) {
+    int which = w / (kk * kNS), pq = (w / kNS) % kk, s = w % kNS;
+    const double* PD = which == 0 ? r.PDc : which == 1 ? r.PDp : r.QD;
+    const double* PB = which == 0 ? r.PBc : which == 1 ? r.PBp : r.QB;
+    double acc[kNJ] = {0.0, 0.0, 0.0};
+    if (which == 2 || a.grad) {
+      for (int t = 0; t < nt; ++t) {
+        double sd = 0.0;
+        const double* pd = PD + (((int64_t)t * kk + pq) * pch) * kNP + s;
+        for (int c = 0; c < pch; ++c) sd += pd[c * kNP];
+        for (int j = 0; j < kNJ; ++j) acc[j] = fma(a.m_diag[j * nt + t], sd, acc[j]);
+        if (t + 1 < nt) {
+          double sb = 0.0;
+          const double* pb = PB + (((int64_t)t * kk + pq) * pch) * kNP + s;
+          for (int c = 0; c < pch; ++c) sb += pb[c * kNP];
+          for (int j = 0; j < kNJ; ++j)
+            acc[j] = fma(2.0 * a.m_sub[j * (nt - 1) + t], sb, acc[j]);
+        }
+      }
+    }
+    for (int j = 0; j < kNJ; ++j) {
+      if (which == 0) RDc[j][pq][s] = acc[j];
+      else if (which == 1) RDp[j][pq][s] = acc[j];
+      else RX[j][pq][s] = acc[j];
+    }
+  }
+  if (tid < a.k) {
+    int m = tid;
+    double cnt = 0.0, pc = 0.0, tt = 0.0, rs = 0.0;
+    if (a.grad) {
+      int mm = m * a.k + m;
+      for (int t = 0; t < nt; ++t) {
+        const double* pd = r.PDc + (((int64_t)t * kk + mm) * pch) * kNP + 3;
+        for (int c = 0; c < pch; ++c) cnt += pd[c * kNP];
+        if (a.a > 0) {
+          const double* pcp = r.PCc + ((int64_t)t * a.k + m) * a.ach;
+          for (int c = 0; c < a.ach; ++c) pc += pcp[c];
+        }
+      }
+      if (a.a > 0) {
+        const double* tr = a.traw + (int64_t)m * a.a * a.a;
+        for (int i = 0; i < a.a * a.a; ++i) tt += r.ZTc[i] * tr[i];
+      }
+    }
+    for (int c = 0; c < a.rch; ++c) rs += r.RS[(int64_t)m * a.rch + c];
+    CNT[m] = cnt; PC[m] = pc; TT[m] = tt; RS[m] = rs;
+  }
+  __syncthreads();
+  if (tid != 0) return;
+  const CoefLayout& L = a.L;
+  const double* th = coefbuf + L.theta;
+  const double* tau = coefbuf + L.tau;
+  const double* coef = coefbuf + L.coef;
+  const double* dcoef = coefbuf + L.dcoef;
+  const int d = a.d, k = a.k;
+  double ldc = 0.0, ldp = 0.0;
+  for (int i = 0; i < a.nldc; ++i) ldc += r.ldc[i];
+  for (int i = 0; i < a.nldp; ++i) ldp += r.ldp[i];
+  ldp += a.a * log(a.tip);
+  double quad = 0.0;
+  for (int pq = 0; pq < kk; ++pq)
+    for (int j = 0; j < kNJ; ++j)
+      for (int s = 0; s < kNS; ++s) quad += coef[(pq * kNJ + j) * kNS + s] * RX[j][pq][s];
+  const double* beta = r.x + (int64_t)nt * a.ld;
+  for (int i = 0; i < a.a; ++i) quad += a.tip * beta[i] * beta[i];
+  double ll = 0.0, lp = 0.0;
+  for (int m = 0; m < k; ++m) ll += 0.5 * a.n_var[m] * log(tau[m]) - 0.5 * tau[m] * RS[m];
+  for (int i = 0; i < d; ++i) lp -= th[i] * th[i] / (2.0 * a.pvar);
+  double f = 0.5 * ldp - 0.5 * ldc - 0.5 * quad + ll + lp;
+  int failc = *r.failc, failp = *r.failp;
+  out[0] = f;
+  double* parts = out + 1 + d;
+  parts[0] = ldp; parts[1] = ldc; parts[2] = quad; parts[3] = ll; parts[4] = lp; parts[5] = f;
+  parts[6] = failc; parts[7] = failp;
+  double* ph = parts + kOutParts;
+  const int tau0 = d - k;
+  for (int kp = 0; kp < d; ++kp) {
+    double trc = 0.0, trp = 0.0, qx = 0.0;
+    if (a.grad) {
+      const double* dc = dcoef + (int64_t)kp * kk * kNJ * kNS;
+      for (int pq = 0; pq < kk; ++pq)
+        for (int j = 0; j < kNJ; ++j)
+          for (int s = 0; s < kNS; ++s) {
+            double w = dc[(pq * kNJ + j) * kNS + s];
+            trc += w * RDc[j][pq][s];
+            trp += w * RDp[j][pq][s];
+            qx += w * RX[j][pq][s];
+          }
+    }
+    double expl = -th[kp] / a.pvar;
+    if (kp >= tau0) {
+      int m = kp - tau0;
+      trc += tau[m] * (CNT[m] + 2.0 * PC[m] + TT[m]);
+      expl += 0.5 * a.n_var[m] - 0.5 * tau[m] * RS[m];
+    }
+    double pa = -0.5 * trc, pb = -0.5 * qx, pcc = 0.5 * trp;
+    ph[kp] = pa;
+    ph[d + kp] = pb;
+    ph[2 * d + kp] = pcc;
+    ph[3 * d + kp] = expl;
+    out[1 + kp] = a.grad ? pa + pb + pcc + expl : 0.0;
+  }
+}
+
+}  // namespace
+
+int pattern_chunks(const ModelDev& md) { return cdiv(md.nnz, RT); }
+int arrow_chunks(const ModelDev& md) { return cdiv((int64_t)md.a_r * md.ns, RT); }
+int resid_chunks(const ModelDev& md) {
+  return (int)std::max<int64_t>(1, std::min<int64_t>(2048, (md.n_obs + RT - 1) / RT));
+}
+
+bta_status launch_pattern_dot(const ModelDev& md, const double* Z, int with_counts, int t,
+                              double* out, cudaStream_t s) {
+  PatArgs a{md.k, md.ns, md.ld, md.nnz, md.row_of, md.col, md.val,
+            with_counts ? md.cnt + (int64_t)t * md.ld : nullptr};
+  pattern_dot_kernel<<<dim3(pattern_chunks(md), md.k * md.k), RT, 0, s>>>(a, Z, out);
+  BTA_LAUNCHED();
+  return BTA_OK;
+}
+
+bta_status launch_pattern_quad(const ModelDev& md, const double* xr, const double* xc,
+                               double* out, cudaStream_t s) {
+  PatArgs a{md.k, md.ns, md.ld, md.nnz, md.row_of, md.col, md.val, nullptr};
+  pattern_quad_kernel<<<dim3(pattern_chunks(md), md.k * md.k), RT, 0, s>>>(a, xr, xc, out);
+  BTA_LAUNCHED();
+  return BTA_OK;
+}
+
+bta_status launch_arrow_dot(const ModelDev& md, const double* ZC, int t, double* out,
+                            cudaStream_t s) {
+  arrow_dot_kernel<<<dim3(arrow_chunks(md), md.k), RT, 0, s>>>(
+      md.ns, md.a, md.a_r, ZC, md.craw + (int64_t)t * md.a * md.ld, out);
+  BTA_LAUNCHED();
+  return BTA_OK;
+}
+
+bta_status launch_residual(const ModelDev& md, const double* x, double* out, cudaStream_t s) {
+  int ch = resid_chunks(md);
+  int per = (int)((md.n_obs + ch - 1) / ch);
+  residual_kernel<<<ch, RT, 0, s>>>(md.n_obs, per, md.k, md.a_r, (int64_t)md.nt * md.ld,
+                                    md.obs_lat, md.obs_v, md.obs_cov, md.y, x, out);
+  BTA_LAUNCHED();
+  return BTA_OK;
+}
+
+bta_status launch_finalize(const ModelDev& md, const CoefLayout& L, const double* coefbuf,
+                           const Reductions& r, double* out, cudaStream_t s) {
+  FinArgs a{};
+  a.k = md.k; a.d = md.d; a.nt = md.nt; a.a = md.a; a.a_r = md.a_r; a.ld = md.ld;
+  a.kk = md.k * md.k; a.pch = pattern_chunks(md); a.ach = arrow_chunks(md);
+  a.rch = resid_chunks(md); a.nldc = r.nldc; a.nldp = r.nldp; a.grad = r.grad;
+  a.tip = md.tip_prior; a.pvar = md.theta_prior_var;
+  a.m_diag = md.m_diag; a.m_sub = md.m_sub; a.traw = md.traw;
+  for (int m = 0; m < kMaxK; ++m) a.n_var[m] = m < md.k ? md.n_per_var[m] : 0.0;
+  a.L = L; a.r = r;
+  finalize_kernel<<<1, RT, 0, s>>>(a, coefbuf, out);
+  BTA_LAUNCHED();
+  return BTA_OK;
+}
+
+}  // namespace bta

@@ -1,0 +1,36 @@
+// Block sweeps over a BTA descriptor (sweep.cu).
+#pragma once
+
+#include "model.cuh"
+
+namespace bta {
+
+// Scratch for one sweep: three ld x ld blocks, the diagonal-factor scratch,
+// two a x ld arrow blocks, GEMV partials and the arrow accumulator v_T.
+struct SweepWs {
+  double *W1 = nullptr, *W2 = nullptr, *W3 = nullptr, *pot = nullptr;
+  double *Wc1 = nullptr, *Wc2 = nullptr, *gv = nullptr, *vT = nullptr;
+  static size_t bytes(int ld, int a);
+  void carve(double* base, int ld, int a);
+};
+
+// Fused Eq. 7 reductions for the selected-inversion sweep.
+struct SelinvFuse {
+  const ModelDev* md = nullptr;
+  int counts = 0;          // add the observation-count diagonal (Q_c)
+  double* PD = nullptr;    // [nt][kk][pchunks][kNP]
+  double* PB = nullptr;    // [nt-1][kk][pchunks][kNP]
+  double* PC = nullptr;    // [nt][k][achunks] or null
+};
+
+int logdet_slots(int n, int ld);   // n * (ld / 32) + 1 (tip)
+
+bta_status factor_sweep(const bta_desc& q, double* rhs, double* slots, int32_t* fail,
+                        const SweepWs& ws, cudaStream_t s);
+bta_status lower_solve(const bta_desc& q, double* z, const SweepWs& ws, cudaStream_t s);
+bta_status upper_solve(const bta_desc& q, double* z, const SweepWs& ws, cudaStream_t s);
+bta_status tip_forward(const bta_desc& q, double* rT, const double* vT, cudaStream_t s);
+bta_status selinv_sweep(const bta_desc& q, const SweepWs& ws, const SelinvFuse* fuse,
+                        cudaStream_t s);
+
+}  // namespace bta
