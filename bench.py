@@ -171,6 +171,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fd-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--nt", type=int, default=0,
+                    help="override the number of time blocks (profiling a shorter copy of "
+                         "the same model: identical per-block kernels)")
+    ap.add_argument("--mode", default="full", choices=["full", "gemm"],
+                    help="gemm: only the dominant kernel at the sweep's block shape "
+                         "(the small case used for ncu captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -192,7 +198,14 @@ def main():
     import paper_2605_06392_gb300 as P
     import workloads
 
-    prob = workloads.make_problem(WORKLOAD)
+    if args.mode == "gemm":
+        b = workloads.WORKLOADS[WORKLOAD]["nx"] * workloads.WORKLOADS[WORKLOAD]["ny"]
+        ms, tf = gemm_roofline(P, torch, b, reps=args.steps)
+        print(json.dumps({"kernel": "gemm_f64_kernel", "shape": [b, b, b], "launch_ms": ms,
+                          "tflops": tf, "frac": tf / FP64_PEAK_TFLOPS}), flush=True)
+        return
+
+    prob = workloads.make_problem(WORKLOAD, **({"nt": args.nt} if args.nt else {}))
     model = P.InlaModel(prob)
     theta = prob.theta.copy()
     stream = torch.cuda.current_stream()
@@ -213,6 +226,7 @@ def main():
     k0 = model.kernel_launches()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     host_times = []
+    torch.cuda.cudart().cudaProfilerStart()         # profiler range = the timed steps
     e0.record(stream)
     for _ in range(args.steps):
         t0 = time.perf_counter()
@@ -220,6 +234,7 @@ def main():
         host_times.append(time.perf_counter() - t0)
     e1.record(stream)
     e1.synchronize()
+    torch.cuda.cudart().cudaProfilerStop()
     barrier()
     clocks.stop()
     launches = model.kernel_launches() - k0
@@ -236,13 +251,15 @@ def main():
 
     # --- FD baseline: 2d+1 value-only evaluations per gradient, same GPU
     pts = workloads.fd_stencil(theta, 1e-3)
-    model.value_and_grad(pts[:2], grad=False)       # warm the value-only graph
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.fd_steps):
-        fv, _ = model.value_and_grad(pts, grad=False)
-    t_fd = (time.perf_counter() - t0) / args.fd_steps
-    g_fd = (fv[1::2] - fv[2::2]) / 2e-3
+    t_fd, g_fd = float("nan"), np.full(prob.d, np.nan)
+    if args.fd_steps > 0:
+        model.value_and_grad(pts[:2], grad=False)       # warm the value-only graph
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.fd_steps):
+            fv, _ = model.value_and_grad(pts, grad=False)
+        t_fd = (time.perf_counter() - t0) / args.fd_steps
+        g_fd = (fv[1::2] - fv[2::2]) / 2e-3
 
     # --- dominant kernel roofline
     gemm_ms, gemm_tf = gemm_roofline(P, torch, prob.b)
@@ -260,7 +277,8 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": "32x32", "b": prob.b, "ld": model.ld,
+            "config": {"workload": WORKLOAD if not args.nt else f"{WORKLOAD}_nt{args.nt}",
+                       "grid": "32x32", "b": prob.b, "ld": model.ld,
                        "nt": prob.nt, "a": prob.a, "d": prob.d, "n_obs": prob.n_obs,
                        "l2": "working set 1.7 GB > L2, no flush", "parallelism": "replicas"},
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 8 * prob.d,
@@ -274,9 +292,11 @@ def main():
                                                                   np.maximum(np.abs(g), 1.0)))},
             "fp64_step": {"algorithmic_tflop_per_step": flops_grad / 1e12,
                           "achieved_tflops": step_tf, "frac_of_peak": step_tf / FP64_PEAK_TFLOPS},
-            "roofline": {"bound": "alu", "kernel": "gemm_f64_kernel<64,64> (b x b x b)",
+            "roofline": {"bound": "alu", "kernel": "gemm_f64_kernel<32,32> at b x b x b",
                          "achieved": gemm_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": gemm_tf / FP64_PEAK_TFLOPS, "traffic": None,
+                         "frac": gemm_tf / FP64_PEAK_TFLOPS, "traffic": 16.8e6,
+                         "traffic_source": "ncu dram__bytes_read+write per launch, "
+                                           "profiles/gemm_f64_block1024.md",
                          "launch_ms": gemm_ms,
                          "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz"},
             "clocks": clocks.summary(),

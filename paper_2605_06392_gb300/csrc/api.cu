@@ -275,10 +275,10 @@ static bta_status model_create_impl(const inla_model_spec* sp, inla_model* m) {
   BTA_TRY(upload(m, &md.row_of, row_of.data(), sp->nnz));
   BTA_TRY(upload(m, &md.val, val.data(), val.size()));
   md.m_diag_h.assign(sp->m_diag, sp->m_diag + 3 * nt);
-  md.m_sub_h.assign(3 * std::max(nt - 1, 0), 0.0);
+  md.m_sub_h.assign(std::max(3 * (nt - 1), 1), 0.0);
   if (nt > 1) std::memcpy(md.m_sub_h.data(), sp->m_sub, 3 * (nt - 1) * sizeof(double));
   BTA_TRY(upload(m, &md.m_diag, md.m_diag_h.data(), md.m_diag_h.size()));
-  BTA_TRY(upload(m, &md.m_sub, md.m_sub_h.data(), std::max<size_t>(md.m_sub_h.size(), 1)));
+  BTA_TRY(upload(m, &md.m_sub, md.m_sub_h.data(), md.m_sub_h.size()));
   // --- observation-derived, theta-independent pieces (fixed accumulation order)
   std::vector<double> cnt((size_t)nt * ld, 0.0), craw((size_t)nt * a * ld, 0.0),
       traw((size_t)k * a * a, 0.0), rraw((size_t)nt * ld + a, 0.0);
