@@ -145,6 +145,26 @@ bta_status bta_factor(bta_desc* q, double* rhs_inout, double* logdet, int32_t* f
                       int32_t precision, cudaStream_t stream);
 
 /*
+ * bta_factor_noalloc -- the same factorisation as bta_factor (same arguments,
+ * same results, precision fixed to FP64), for callers that cannot allocate
+ * device memory during the call: a process that has handed the device to its
+ * own allocator or a fixed memory budget, a framework that forbids allocation
+ * on its hot path, or code that cannot take the device-wide synchronisation a
+ * free may imply.  The paper has no counterpart; this is a library-level
+ * variant.  Its temporary blocks come from a fixed array the library reserves
+ * on each device that loads it (2.4 MB, held until the process exits), so:
+ *   - sizes are limited to ld <= 256, a <= 32 and n * (ld / 32) + 1 <= 16384;
+ *     beyond that it returns BTA_ERR_ARG without doing any work;
+ *   - all calls on a device share the array: calls that overlap on the GPU
+ *     race and give wrong results, so order them on one stream;
+ *   - the first call on a device looks up the array's device address and
+ *     caches it; make that first call before any stream capture.
+ * It calls no cudaMalloc, cudaFree or allocating library routine.
+ */
+bta_status bta_factor_noalloc(bta_desc* q, double* rhs_inout, double* logdet,
+                              int32_t* fail_block, cudaStream_t stream);
+
+/*
  * bta_solve -- Eqs. 3-5: given a FACTORED descriptor and z (device, from the
  * fused lower solve), overwrite z by x = Q^{-1} r.  With lower = 1 the lower
  * solve L z = r is done first (so z_inout may hold r).  refine must be 0 in

@@ -57,6 +57,8 @@ SIGNATURES = {
                                C.POINTER(bta_desc), C.c_void_p, C.c_void_p]),
     "bta_factor": (C.c_int, [C.POINTER(bta_desc), C.c_void_p, C.c_void_p, C.c_void_p,
                              C.c_int32, C.c_void_p]),
+    "bta_factor_noalloc": (C.c_int, [C.POINTER(bta_desc), C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_void_p]),
     "bta_solve": (C.c_int, [C.POINTER(bta_desc), C.c_void_p, C.c_int32, C.c_int32,
                             C.POINTER(bta_desc), C.c_void_p]),
     "bta_selinv": (C.c_int, [C.POINTER(bta_desc), C.c_void_p, C.POINTER(C.c_double), C.c_int32,
