@@ -23,65 +23,80 @@ namespace {
 
 constexpr int T = kPad;   // leaf size
 
-__global__ void __launch_bounds__(256) potrf_inv_leaf(double* A, int ld, double* logdet_slot,
-                                                      int32_t* fail, int32_t fail_code) {
-  __shared__ double L[T][T + 1];
-  __shared__ double W[T][T + 1];
-  __shared__ int bad;
+// 32 x 32 leaf: A = L1 D L1^T (unit-lower L1) by right-looking elimination,
+// with the inverse X = L1^{-1} built in the same steps (Gauss-Jordan on the
+// unit factor), then L^{-1} = D^{-1/2} X and log|A| = sum log D_j.  Step j
+// reads only column j of the trailing matrix and row j of X, both final at
+// the end of step j-1, and writes only positions right of column j or below
+// row j, so one barrier per step suffices.  Each of the 128 threads owns a
+// fixed set of lower-triangle positions (i, k) and updates each of them once
+// per step while i > j: the trailing matrix if k > j, X if k <= j.
+constexpr int kLeafThreads = 128;
+constexpr int kLeafPos = T * (T + 1) / 2;
+constexpr int kLeafPer = (kLeafPos + kLeafThreads - 1) / kLeafThreads;
+
+__global__ void __launch_bounds__(kLeafThreads) potrf_inv_leaf(double* A, int ld,
+                                                               double* logdet_slot, int32_t* fail,
+                                                               int32_t fail_code) {
+  __shared__ double S[T][T + 1];
+  __shared__ double X[T][T + 1];
   const int tid = threadIdx.x;
-  for (int e = tid; e < T * T; e += blockDim.x) {
-    int i = e % T, j = e / T;
-    L[i][j] = (i >= j) ? A[i + (int64_t)j * ld] : 0.0;
+  int pi[kLeafPer], pk[kLeafPer];
+#pragma unroll
+  for (int r = 0; r < kLeafPer; ++r) {
+    int p = tid + kLeafThreads * r;
+    if (p < kLeafPos) {
+      int i = 0;
+      while ((i + 1) * (i + 2) / 2 <= p) ++i;
+      pi[r] = i;
+      pk[r] = p - i * (i + 1) / 2;
+    } else {
+      pi[r] = -1;
+      pk[r] = 0;
+    }
   }
-  if (tid == 0) bad = 0;
+  for (int e = tid; e < T * T; e += kLeafThreads) {
+    int i = e % T, j = e / T;
+    S[i][j] = (i >= j) ? A[i + (int64_t)j * ld] : 0.0;
+    X[i][j] = (i == j) ? 1.0 : 0.0;
+  }
   __syncthreads();
-  // Right-looking Cholesky of the leaf.
   for (int j = 0; j < T; ++j) {
+    const double invd = 1.0 / S[j][j];
+#pragma unroll
+    for (int r = 0; r < kLeafPer; ++r) {
+      const int i = pi[r], k = pk[r];
+      if (i > j) {
+        const double lij = S[i][j] * invd;
+        if (k > j) S[i][k] = fma(-lij, S[k][j], S[i][k]);
+        else X[i][k] = fma(-lij, X[j][k], X[i][k]);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < kLeafPer; ++r) {
+    const int i = pi[r], k = pk[r];
+    if (i >= 0) A[i + (int64_t)k * ld] = X[i][k] / sqrt(S[i][i]);
+  }
+  if (tid < 32) {
+    const double dj = S[tid][tid];
+    const bool bad = !(dj > 0.0) || !isfinite(dj);
+    double l = bad ? 0.0 : log(dj);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
+    const unsigned anybad = __ballot_sync(0xffffffffu, bad);
     if (tid == 0) {
-      double d = L[j][j];
-      if (!(d > 0.0) || !isfinite(d)) { bad = 1; d = 1.0; }
-      L[j][j] = sqrt(d);
+      *logdet_slot = l;
+      if (anybad) atomicCAS(fail, -1, fail_code);
     }
-    __syncthreads();
-    double piv = L[j][j];
-    for (int i = j + 1 + tid; i < T; i += blockDim.x) L[i][j] /= piv;
-    __syncthreads();
-    // trailing update of the lower triangle, columns j+1..T-1
-    int rem = T - j - 1;
-    for (int e = tid; e < rem * rem; e += blockDim.x) {
-      int i = j + 1 + e % rem, k = j + 1 + e / rem;
-      if (i >= k) L[i][k] = fma(-L[i][j], L[k][j], L[i][k]);
-    }
-    __syncthreads();
-  }
-  // Inverse of the lower-triangular leaf: thread c forms column c.
-  if (tid < T) {
-    int c = tid;
-    for (int i = 0; i < c; ++i) W[i][c] = 0.0;
-    W[c][c] = 1.0 / L[c][c];
-    for (int i = c + 1; i < T; ++i) {
-      double s = 0.0;
-      for (int k = c; k < i; ++k) s = fma(L[i][k], W[k][c], s);
-      W[i][c] = -s / L[i][i];
-    }
-  }
-  __syncthreads();
-  for (int e = tid; e < T * T; e += blockDim.x) {
-    int i = e % T, j = e / T;
-    if (i >= j) A[i + (int64_t)j * ld] = W[i][j];
-  }
-  if (tid == 0) {
-    double s = 0.0;
-    for (int j = 0; j < T; ++j) s += log(L[j][j]);
-    *logdet_slot = 2.0 * s;
-    if (bad) atomicCAS(fail, -1, fail_code);
   }
 }
 
 bta_status rec(double* A, int n, int ld, double* scratch, double* slots, int32_t* fail,
                int32_t fail_code, cudaStream_t s) {
   if (n == T) {
-    potrf_inv_leaf<<<1, 256, 0, s>>>(A, ld, slots, fail, fail_code);
+    potrf_inv_leaf<<<1, kLeafThreads, 0, s>>>(A, ld, slots, fail, fail_code);
     BTA_LAUNCHED();
     return BTA_OK;
   }
