@@ -251,7 +251,7 @@ def main():
 
     # --- FD baseline: 2d+1 value-only evaluations per gradient, same GPU
     pts = workloads.fd_stencil(theta, 1e-3)
-    t_fd, g_fd = float("nan"), np.full(prob.d, np.nan)
+    t_fd, g_fd, t_fdb = float("nan"), np.full(prob.d, np.nan), float("nan")
     if args.fd_steps > 0:
         model.value_and_grad(pts[:2], grad=False)       # warm the value-only graph
         torch.cuda.synchronize()
@@ -260,6 +260,13 @@ def main():
             fv, _ = model.value_and_grad(pts, grad=False)
         t_fd = (time.perf_counter() - t0) / args.fd_steps
         g_fd = (fv[1::2] - fv[2::2]) / 2e-3
+        # batched: all 2d+1 evaluations swept together in the same launches
+        model.value_and_grad(pts, grad=False, concurrent=pts.shape[0])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.fd_steps):
+            fvb, _ = model.value_and_grad(pts, grad=False, concurrent=pts.shape[0])
+        t_fdb = (time.perf_counter() - t0) / args.fd_steps
 
     # --- dominant kernel roofline
     gemm_ms, gemm_tf = gemm_roofline(P, torch, prob.b)
@@ -288,6 +295,8 @@ def main():
                             "gradients_per_s": 1.0 / t_fd,
                             "speedup_ad_vs_fd": t_fd / t_step,
                             "c_ad": t_step / (t_fd / pts.shape[0]),
+                            "batched_seconds_per_gradient": t_fdb,
+                            "speedup_ad_vs_batched_fd": t_fdb / t_step,
                             "max_rel_diff_fd_vs_ad": float(np.max(np.abs(g_fd - g) /
                                                                   np.maximum(np.abs(g), 1.0)))},
             "fp64_step": {"algorithmic_tflop_per_step": flops_grad / 1e12,

@@ -104,7 +104,9 @@ typedef struct inla_model inla_model;
 typedef struct {
   int32_t precision;   /* 0: FP64 everywhere (the only mode in this build)  */
   int32_t use_graph;   /* 1: capture the evaluation in a CUDA graph, replay */
-  int32_t streams;     /* concurrent evaluations for batch > 1 (>= 1)       */
+  int32_t streams;     /* thetas evaluated together for batch > 1 (1..16): their
+                          matrices are swept in the same batched launches;
+                          each needs its own device buffers                 */
   int32_t reserved;
 } inla_opts;
 

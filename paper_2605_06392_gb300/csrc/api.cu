@@ -23,12 +23,8 @@
 
 using namespace bta;
 
-struct inla_model {
-  ModelDev md;
-  CoefLayout L;
-  int n = 0, b = 0, ld = 0, a = 0, d = 0;
-  int nslots = 0, nslots_p = 0;
-  // device buffers (model-owned)
+// One evaluation context: everything a single theta's evaluation writes.
+struct EvalCtx {
   double* coefbuf = nullptr;
   bta_desc qc{}, qp{};
   double* x = nullptr;          // r -> z -> x*  (n*ld + a)
@@ -38,20 +34,33 @@ struct inla_model {
   double *PDc = nullptr, *PBc = nullptr, *PCc = nullptr, *PDp = nullptr, *PBp = nullptr;
   double *QD = nullptr, *QB = nullptr, *RS = nullptr;
   double* out = nullptr;
-  double* wsbuf = nullptr;
   SweepWs wsc, wsp;
+  SelinvFuse fc, fp;
+  int have_factors = 0;         // last evaluation was value-only: factors still held
+};
+
+struct GraphKey {
+  int mode, count;
+  cudaGraphExec_t exec;
+  int64_t kernels;
+};
+
+struct inla_model {
+  ModelDev md;
+  CoefLayout L;
+  int n = 0, b = 0, ld = 0, a = 0, d = 0;
+  int nslots = 0;
+  std::vector<EvalCtx> ctx;     // grown on demand (batched evaluations)
   std::vector<void*> allocs;
   // host
-  double* hout = nullptr;       // pinned
-  double* htheta = nullptr;     // pinned
-  std::vector<double> last;
-  // concurrency
-  cudaStream_t s1 = nullptr, s2 = nullptr;
-  cudaEvent_t ev0 = nullptr, evx = nullptr, ev1 = nullptr, ev2 = nullptr;
-  cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};   // value, value+grad, backward
-  int64_t graph_kernels[3] = {0, 0, 0};
-  int have_factors = 0;         // last evaluation was value-only: factors still held
+  double* hout = nullptr;       // pinned, kMaxBatch outputs
+  double* htheta = nullptr;     // pinned, kMaxBatch thetas
+  std::vector<double> last;     // output of the last single evaluation
+  std::vector<GraphKey> graphs;
   int64_t launched = 0;         // kernels this model ran (graph replays included)
+  // the Q_c set and the Q_p set are swept on two streams (fork/join by events)
+  cudaStream_t s1 = nullptr, s2 = nullptr;
+  cudaEvent_t ev0 = nullptr, evx = nullptr, ev1 = nullptr, ev2 = nullptr, evd = nullptr;
 };
 
 namespace {
@@ -83,128 +92,184 @@ bool finite_theta(const double* th, int d) {
   return true;
 }
 
-// Record one evaluation (grad = 0/1) on stream s0; theta already in coefbuf.
-bta_status record_eval(inla_model* m, int grad, cudaStream_t s0) {
+// Allocate evaluation context c (buffers for Q_c, Q_p, x*, reductions).
+bta_status ctx_alloc(inla_model* m, EvalCtx& c) {
   const ModelDev& md = m->md;
-  const int n = m->n, ld = m->ld, kk = md.k * md.k, pch = pattern_chunks(md);
-  BTA_TRY(launch_coef(md, m->L, m->coefbuf, s0));
-  BTA_CUDA_TRY(cudaMemsetAsync(m->fail, 0xff, 2 * sizeof(int32_t), s0));
-  BTA_CUDA_TRY(cudaEventRecord(m->ev0, s0));
-  // ---- stream 1: Q_c
-  BTA_CUDA_TRY(cudaStreamWaitEvent(m->s1, m->ev0, 0));
-  m->qc.state = BTA_STATE_EMPTY;
-  BTA_TRY(launch_assemble(md, m->L, m->coefbuf, 1, m->qc, m->x, m->s1));
-  BTA_TRY(factor_sweep(m->qc, m->x, m->slots_c, m->fail, m->wsc, m->s1));
-  BTA_TRY(upper_solve(m->qc, m->x, m->wsc, m->s1));
-  BTA_CUDA_TRY(cudaEventRecord(m->evx, m->s1));
-  BTA_TRY(launch_residual(md, m->x, m->RS, m->s1));
-  if (grad) {
-    SelinvFuse fz;
-    fz.md = &md; fz.counts = 1; fz.PD = m->PDc; fz.PB = m->PBc; fz.PC = m->PCc;
-    BTA_TRY(selinv_sweep(m->qc, m->wsc, &fz, m->s1));
-  }
-  BTA_CUDA_TRY(cudaEventRecord(m->ev1, m->s1));
-  // ---- stream 2: Q_p
-  BTA_CUDA_TRY(cudaStreamWaitEvent(m->s2, m->ev0, 0));
-  BTA_TRY(launch_assemble(md, m->L, m->coefbuf, 0, m->qp, nullptr, m->s2));
-  BTA_TRY(factor_sweep(m->qp, nullptr, m->slots_p, m->fail + 1, m->wsp, m->s2));
-  BTA_CUDA_TRY(cudaStreamWaitEvent(m->s2, m->evx, 0));
-  for (int t = 0; t < n; ++t) {
-    const double* xt = m->x + (int64_t)t * ld;
-    BTA_TRY(launch_pattern_quad(md, xt, xt, m->QD + (int64_t)t * kk * pch * kNP, m->s2));
-    if (t + 1 < n)
-      BTA_TRY(launch_pattern_quad(md, xt + ld, xt, m->QB + (int64_t)t * kk * pch * kNP, m->s2));
-  }
-  if (grad) {
-    SelinvFuse fz;
-    fz.md = &md; fz.counts = 0; fz.PD = m->PDp; fz.PB = m->PBp; fz.PC = nullptr;
-    BTA_TRY(selinv_sweep(m->qp, m->wsp, &fz, m->s2));
-  }
-  BTA_CUDA_TRY(cudaEventRecord(m->ev2, m->s2));
-  // ---- join
-  BTA_CUDA_TRY(cudaStreamWaitEvent(s0, m->ev1, 0));
-  BTA_CUDA_TRY(cudaStreamWaitEvent(s0, m->ev2, 0));
-  Reductions r{};
-  r.PDc = m->PDc; r.PBc = m->PBc; r.PCc = m->PCc; r.ZTc = m->qc.T;
-  r.PDp = m->PDp; r.PBp = m->PBp; r.QD = m->QD; r.QB = m->QB; r.RS = m->RS;
-  r.ldc = m->slots_c; r.nldc = m->nslots; r.ldp = m->slots_p; r.nldp = m->nslots_p;
-  r.failc = m->fail; r.failp = m->fail + 1; r.x = m->x; r.grad = grad;
-  BTA_TRY(launch_finalize(md, m->L, m->coefbuf, r, m->out, s0));
+  const int nt = md.nt, ld = md.ld, a = md.a, k = md.k;
+  const size_t blk = (size_t)ld * ld;
+  BTA_TRY(dmalloc(m, &c.coefbuf, m->L.total));
+  c.qc.n = nt; c.qc.b = md.b; c.qc.a = a; c.qc.ld = ld;
+  BTA_TRY(dmalloc(m, &c.qc.D, nt * blk));
+  BTA_TRY(dmalloc(m, &c.qc.B, std::max(nt - 1, 1) * blk));
+  BTA_TRY(dmalloc(m, &c.qc.C, std::max<size_t>((size_t)nt * a * ld, 1)));
+  BTA_TRY(dmalloc(m, &c.qc.T, std::max(a * a, 1)));
+  c.qp = c.qc;
+  c.qp.a = 0; c.qp.C = nullptr; c.qp.T = nullptr;
+  BTA_TRY(dmalloc(m, &c.qp.D, nt * blk));
+  BTA_TRY(dmalloc(m, &c.qp.B, std::max(nt - 1, 1) * blk));
+  BTA_TRY(dmalloc(m, &c.x, (size_t)nt * ld + a));
+  BTA_TRY(dmalloc(m, &c.slots_c, m->nslots));
+  BTA_TRY(dmalloc(m, &c.slots_p, m->nslots));
+  BTA_TRY(dmalloc(m, &c.fail, 2));
+  const size_t pblk = (size_t)k * k * pattern_chunks(md) * kNP;
+  BTA_TRY(dmalloc(m, &c.PDc, nt * pblk));
+  BTA_TRY(dmalloc(m, &c.PBc, std::max(nt - 1, 1) * pblk));
+  BTA_TRY(dmalloc(m, &c.PCc, std::max<size_t>((size_t)nt * k * arrow_chunks(md), 1)));
+  BTA_TRY(dmalloc(m, &c.PDp, nt * pblk));
+  BTA_TRY(dmalloc(m, &c.PBp, std::max(nt - 1, 1) * pblk));
+  BTA_TRY(dmalloc(m, &c.QD, nt * pblk));
+  BTA_TRY(dmalloc(m, &c.QB, std::max(nt - 1, 1) * pblk));
+  // residual_kernel writes kMaxK rows
+  BTA_TRY(dmalloc(m, &c.RS, (size_t)kMaxK * resid_chunks(md)));
+  BTA_TRY(dmalloc(m, &c.out, out_size(md.d)));
+  const size_t wsb = SweepWs::bytes(ld, a) / sizeof(double);
+  double* wsbuf = nullptr;
+  BTA_TRY(dmalloc(m, &wsbuf, 2 * wsb));
+  c.wsc.carve(wsbuf, ld, a);
+  c.wsp.carve(wsbuf + wsb, ld, a);
+  c.fc.md = &m->md; c.fc.counts = 1; c.fc.PD = c.PDc; c.fc.PB = c.PBc; c.fc.PC = c.PCc;
+  c.fp.md = &m->md; c.fp.counts = 0; c.fp.PD = c.PDp; c.fp.PB = c.PBp; c.fp.PC = nullptr;
   return BTA_OK;
 }
 
-// Backward only: the two selected inversions on the factors a value-only
-// evaluation left in place, then the final combination with grad on.
-bta_status record_backward(inla_model* m, cudaStream_t s0) {
-  const ModelDev& md = m->md;
-  BTA_CUDA_TRY(cudaEventRecord(m->ev0, s0));
-  BTA_CUDA_TRY(cudaStreamWaitEvent(m->s1, m->ev0, 0));
-  SelinvFuse fc;
-  fc.md = &md; fc.counts = 1; fc.PD = m->PDc; fc.PB = m->PBc; fc.PC = m->PCc;
-  BTA_TRY(selinv_sweep(m->qc, m->wsc, &fc, m->s1));
-  BTA_CUDA_TRY(cudaEventRecord(m->ev1, m->s1));
-  BTA_CUDA_TRY(cudaStreamWaitEvent(m->s2, m->ev0, 0));
-  SelinvFuse fp;
-  fp.md = &md; fp.counts = 0; fp.PD = m->PDp; fp.PB = m->PBp; fp.PC = nullptr;
-  BTA_TRY(selinv_sweep(m->qp, m->wsp, &fp, m->s2));
-  BTA_CUDA_TRY(cudaEventRecord(m->ev2, m->s2));
-  BTA_CUDA_TRY(cudaStreamWaitEvent(s0, m->ev1, 0));
-  BTA_CUDA_TRY(cudaStreamWaitEvent(s0, m->ev2, 0));
-  Reductions r{};
-  r.PDc = m->PDc; r.PBc = m->PBc; r.PCc = m->PCc; r.ZTc = m->qc.T;
-  r.PDp = m->PDp; r.PBp = m->PBp; r.QD = m->QD; r.QB = m->QB; r.RS = m->RS;
-  r.ldc = m->slots_c; r.nldc = m->nslots; r.ldp = m->slots_p; r.nldp = m->nslots_p;
-  r.failc = m->fail; r.failp = m->fail + 1; r.x = m->x; r.grad = 1;
-  BTA_TRY(launch_finalize(md, m->L, m->coefbuf, r, m->out, s0));
+bta_status ensure_ctx(inla_model* m, int count) {
+  if ((int)m->ctx.size() >= count) return BTA_OK;
+  cudaDeviceSynchronize();
+  m->ctx.reserve(count);
+  while ((int)m->ctx.size() < count) {
+    m->ctx.emplace_back();
+    bta_status st = ctx_alloc(m, m->ctx.back());
+    if (st != BTA_OK) {
+      m->ctx.pop_back();
+      return st;
+    }
+  }
+  // contexts hold pointers to the model: the fuse blocks refer to m->md (stable)
   return BTA_OK;
 }
 
-// mode 0: value, 1: value + grad, 2: backward of the last value-only call.
-bta_status run_eval(inla_model* m, const double* theta, int mode, int use_graph,
-                    cudaStream_t stream) {
-  const int d = m->d;
-  const int grad = mode;
+// Record the evaluation of contexts 0..cnt-1.
+//   mode 0: f only; 1: f and gradient; 2: reverse pass of a preceding mode-0
+//   evaluation (the factors are still in place).
+// The conditional matrices Q_c of all contexts form one set and the priors
+// Q_p another; each set is swept with one batched launch per block step, and
+// the two sets run on two streams.  They are independent until the final
+// combination (the stencil quadratic forms on the Q_p stream wait for x*), so
+// the serial diagonal steps of one set overlap the wide products of the other.
+bta_status record_group(inla_model* m, int mode, int cnt, cudaStream_t s0) {
+  const ModelDev& md = m->md;
+  const int grad = mode >= 1;
+  std::vector<SweepItem> ic(cnt), ip(cnt);
+  for (int e = 0; e < cnt; ++e) {
+    EvalCtx& c = m->ctx[e];
+    ic[e].q = c.qc; ic[e].vec = c.x; ic[e].slots = c.slots_c; ic[e].fail = c.fail;
+    ic[e].ws = c.wsc; ic[e].fuse = &c.fc;
+    ip[e].q = c.qp; ip[e].vec = nullptr; ip[e].slots = c.slots_p; ip[e].fail = c.fail + 1;
+    ip[e].ws = c.wsp; ip[e].fuse = &c.fp;
+  }
   if (mode < 2) {
-    std::memcpy(m->htheta, theta, d * sizeof(double));
-    BTA_CUDA_TRY(cudaMemcpyAsync(m->coefbuf + m->L.theta, m->htheta, d * sizeof(double),
-                                 cudaMemcpyHostToDevice, stream));
+    for (int e = 0; e < cnt; ++e) {
+      EvalCtx& c = m->ctx[e];
+      BTA_TRY(launch_coef(md, m->L, c.coefbuf, s0));
+      BTA_CUDA_TRY(cudaMemsetAsync(c.fail, 0xff, 2 * sizeof(int32_t), s0));
+    }
   }
-  auto rec = [&](cudaStream_t s0) {
-    return mode < 2 ? record_eval(m, mode, s0) : record_backward(m, s0);
-  };
+  BTA_CUDA_TRY(cudaEventRecord(m->ev0, s0));
+  // ---- stream 1: Q_c set
+  BTA_CUDA_TRY(cudaStreamWaitEvent(m->s1, m->ev0, 0));
+  if (mode < 2) {
+    for (int e = 0; e < cnt; ++e)
+      BTA_TRY(launch_assemble(md, m->L, m->ctx[e].coefbuf, 1, m->ctx[e].qc, m->ctx[e].x, m->s1));
+    BTA_TRY(factor_sweep_multi(ic.data(), cnt, m->s1, m->evd));
+    BTA_TRY(upper_solve_multi(ic.data(), cnt, m->s1));
+    BTA_CUDA_TRY(cudaEventRecord(m->evx, m->s1));
+    for (int e = 0; e < cnt; ++e) BTA_TRY(launch_residual(md, m->ctx[e].x, m->ctx[e].RS, m->s1));
+  }
+  if (grad) BTA_TRY(selinv_sweep_multi(ic.data(), cnt, m->s1));
+  BTA_CUDA_TRY(cudaEventRecord(m->ev1, m->s1));
+  // ---- stream 2: Q_p set
+  BTA_CUDA_TRY(cudaStreamWaitEvent(m->s2, m->ev0, 0));
+  if (mode < 2) {
+    for (int e = 0; e < cnt; ++e)
+      BTA_TRY(launch_assemble(md, m->L, m->ctx[e].coefbuf, 0, m->ctx[e].qp, nullptr, m->s2));
+    // start one diagonal step behind the Q_c sweep: the two sweeps then
+    // alternate their latency-bound diagonal factors with wide products
+    BTA_CUDA_TRY(cudaStreamWaitEvent(m->s2, m->evd, 0));
+    BTA_TRY(factor_sweep_multi(ip.data(), cnt, m->s2));
+    BTA_CUDA_TRY(cudaStreamWaitEvent(m->s2, m->evx, 0));
+    for (int e = 0; e < cnt; ++e)
+      BTA_TRY(launch_pattern_quad_all(md, m->ctx[e].x, m->ctx[e].QD, m->ctx[e].QB, m->s2));
+  }
+  if (grad) BTA_TRY(selinv_sweep_multi(ip.data(), cnt, m->s2));
+  BTA_CUDA_TRY(cudaEventRecord(m->ev2, m->s2));
+  // ---- join and combine
+  BTA_CUDA_TRY(cudaStreamWaitEvent(s0, m->ev1, 0));
+  BTA_CUDA_TRY(cudaStreamWaitEvent(s0, m->ev2, 0));
+  for (int e = 0; e < cnt; ++e) {
+    EvalCtx& c = m->ctx[e];
+    Reductions r{};
+    r.PDc = c.PDc; r.PBc = c.PBc; r.PCc = c.PCc; r.ZTc = c.qc.T;
+    r.PDp = c.PDp; r.PBp = c.PBp; r.QD = c.QD; r.QB = c.QB; r.RS = c.RS;
+    r.ldc = c.slots_c; r.nldc = m->nslots; r.ldp = c.slots_p; r.nldp = m->nslots;
+    r.failc = c.fail; r.failp = c.fail + 1; r.x = c.x; r.grad = grad;
+    BTA_TRY(launch_finalize(md, m->L, c.coefbuf, r, c.out, s0));
+  }
+  return BTA_OK;
+}
+
+// Run one group (thetas for contexts 0..cnt-1 already in htheta for mode < 2);
+// outputs land in hout[e * out_size(d)].
+bta_status run_group(inla_model* m, int mode, int cnt, int use_graph, cudaStream_t stream) {
+  const int d = m->d, no = out_size(d);
+  if (mode < 2)
+    for (int e = 0; e < cnt; ++e)
+      BTA_CUDA_TRY(cudaMemcpyAsync(m->ctx[e].coefbuf + m->L.theta, m->htheta + (size_t)e * d,
+                                   d * sizeof(double), cudaMemcpyHostToDevice, stream));
   if (use_graph) {
-    if (!m->gexec[grad]) {
+    GraphKey* gk = nullptr;
+    for (auto& g : m->graphs)
+      if (g.mode == mode && g.count == cnt) gk = &g;
+    if (!gk) {
       const int64_t before = g_launches;
       cudaStream_t cap;
       BTA_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
       BTA_CUDA_TRY(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-      bta_status st = rec(cap);
+      bta_status st = record_group(m, mode, cnt, cap);
       cudaGraph_t graph = nullptr;
       cudaError_t e = cudaStreamEndCapture(cap, &graph);
-      if (st != BTA_OK) { if (graph) cudaGraphDestroy(graph); cudaStreamDestroy(cap); return st; }
+      if (st != BTA_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaStreamDestroy(cap);
+        return st;
+      }
       BTA_CUDA_TRY(e);
-      e = cudaGraphInstantiate(&m->gexec[grad], graph, 0);
+      cudaGraphExec_t exec = nullptr;
+      e = cudaGraphInstantiate(&exec, graph, 0);
       cudaGraphDestroy(graph);
       cudaStreamDestroy(cap);
       BTA_CUDA_TRY(e);
-      m->graph_kernels[grad] = g_launches - before;
+      m->graphs.push_back({mode, cnt, exec, g_launches - before});
+      gk = &m->graphs.back();
     }
-    BTA_CUDA_TRY(cudaGraphLaunch(m->gexec[grad], stream));
-    m->launched += m->graph_kernels[grad];
+    BTA_CUDA_TRY(cudaGraphLaunch(gk->exec, stream));
+    m->launched += gk->kernels;
   } else {
     const int64_t before = g_launches;
-    BTA_TRY(rec(stream));
+    BTA_TRY(record_group(m, mode, cnt, stream));
     m->launched += g_launches - before;
   }
-  const int no = out_size(d);
-  BTA_CUDA_TRY(cudaMemcpyAsync(m->hout, m->out, no * sizeof(double), cudaMemcpyDeviceToHost,
-                               stream));
+  for (int e = 0; e < cnt; ++e)
+    BTA_CUDA_TRY(cudaMemcpyAsync(m->hout + (size_t)e * no, m->ctx[e].out, no * sizeof(double),
+                                 cudaMemcpyDeviceToHost, stream));
   BTA_CUDA_TRY(cudaStreamSynchronize(stream));
-  m->last.assign(m->hout, m->hout + no);
-  m->have_factors = mode == 0;
-  const double* parts = m->hout + 1 + d;
-  if (parts[6] >= 0 || parts[7] >= 0) return BTA_ERR_NOT_SPD;
-  return BTA_OK;
+  bta_status st = BTA_OK;
+  for (int e = 0; e < cnt; ++e) {
+    const double* parts = m->hout + (size_t)e * no + 1 + d;
+    if (parts[6] >= 0 || parts[7] >= 0) st = BTA_ERR_NOT_SPD;
+    m->ctx[e].have_factors = mode == 0;
+  }
+  m->last.assign(m->hout + (size_t)(cnt - 1) * no, m->hout + (size_t)cnt * no);
+  return st;
 }
 
 }  // namespace
@@ -227,14 +292,14 @@ const char* bta_status_string(bta_status s) {
 void inla_model_destroy(inla_model* m) {
   if (!m) return;
   cudaDeviceSynchronize();
-  for (int g = 0; g < 3; ++g)
-    if (m->gexec[g]) cudaGraphExecDestroy(m->gexec[g]);
+  for (auto& g : m->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
   for (void* p : m->allocs) cudaFree(p);
   if (m->hout) cudaFreeHost(m->hout);
   if (m->htheta) cudaFreeHost(m->htheta);
   if (m->s1) cudaStreamDestroy(m->s1);
   if (m->s2) cudaStreamDestroy(m->s2);
-  for (cudaEvent_t e : {m->ev0, m->evx, m->ev1, m->ev2})
+  for (cudaEvent_t e : {m->ev0, m->evx, m->ev1, m->ev2, m->evd})
     if (e) cudaEventDestroy(e);
   delete m;
 }
@@ -316,44 +381,15 @@ static bta_status model_create_impl(const inla_model_spec* sp, inla_model* m) {
   }
   BTA_TRY(upload(m, &md.obs_cov, covv.data(), covv.size()));
   BTA_TRY(upload(m, &md.y, yv.data(), yv.size()));
-  // --- evaluation buffers
+  // --- evaluation buffers: one context up front, more on demand
   m->L.init(k, md.d, nt);
-  BTA_TRY(dmalloc(m, &m->coefbuf, m->L.total));
-  const size_t blk = (size_t)ld * ld;
-  m->qc.n = nt; m->qc.b = b; m->qc.a = a; m->qc.ld = ld;
-  BTA_TRY(dmalloc(m, &m->qc.D, nt * blk));
-  BTA_TRY(dmalloc(m, &m->qc.B, std::max(nt - 1, 1) * blk));
-  BTA_TRY(dmalloc(m, &m->qc.C, std::max<size_t>((size_t)nt * a * ld, 1)));
-  BTA_TRY(dmalloc(m, &m->qc.T, std::max(a * a, 1)));
-  m->qp = m->qc;
-  m->qp.a = 0; m->qp.C = nullptr; m->qp.T = nullptr;
-  BTA_TRY(dmalloc(m, &m->qp.D, nt * blk));
-  BTA_TRY(dmalloc(m, &m->qp.B, std::max(nt - 1, 1) * blk));
-  BTA_TRY(dmalloc(m, &m->x, (size_t)nt * ld + a));
   m->nslots = logdet_slots(nt, ld);
-  m->nslots_p = m->nslots;
-  BTA_TRY(dmalloc(m, &m->slots_c, m->nslots));
-  BTA_TRY(dmalloc(m, &m->slots_p, m->nslots_p));
-  BTA_TRY(dmalloc(m, &m->fail, 2));
-  const size_t pblk = (size_t)k * k * pattern_chunks(md) * kNP;
-  BTA_TRY(dmalloc(m, &m->PDc, nt * pblk));
-  BTA_TRY(dmalloc(m, &m->PBc, std::max(nt - 1, 1) * pblk));
-  BTA_TRY(dmalloc(m, &m->PCc, std::max<size_t>((size_t)nt * k * arrow_chunks(md), 1)));
-  BTA_TRY(dmalloc(m, &m->PDp, nt * pblk));
-  BTA_TRY(dmalloc(m, &m->PBp, std::max(nt - 1, 1) * pblk));
-  BTA_TRY(dmalloc(m, &m->QD, nt * pblk));
-  BTA_TRY(dmalloc(m, &m->QB, std::max(nt - 1, 1) * pblk));
-  BTA_TRY(dmalloc(m, &m->RS, (size_t)kMaxK * resid_chunks(md)));   // residual_kernel writes kMaxK rows
-  BTA_TRY(dmalloc(m, &m->out, out_size(md.d)));
-  size_t wsb = SweepWs::bytes(ld, a) / sizeof(double);
-  BTA_TRY(dmalloc(m, &m->wsbuf, 2 * wsb));
-  m->wsc.carve(m->wsbuf, ld, a);
-  m->wsp.carve(m->wsbuf + wsb, ld, a);
-  BTA_CUDA_TRY(cudaMallocHost(&m->hout, out_size(md.d) * sizeof(double)));
-  BTA_CUDA_TRY(cudaMallocHost(&m->htheta, kMaxD * sizeof(double)));
+  BTA_TRY(ensure_ctx(m, 1));
+  BTA_CUDA_TRY(cudaMallocHost(&m->hout, (size_t)kMaxBatch * out_size(md.d) * sizeof(double)));
+  BTA_CUDA_TRY(cudaMallocHost(&m->htheta, (size_t)kMaxBatch * kMaxD * sizeof(double)));
   BTA_CUDA_TRY(cudaStreamCreateWithFlags(&m->s1, cudaStreamNonBlocking));
   BTA_CUDA_TRY(cudaStreamCreateWithFlags(&m->s2, cudaStreamNonBlocking));
-  for (cudaEvent_t* e : {&m->ev0, &m->evx, &m->ev1, &m->ev2})
+  for (cudaEvent_t* e : {&m->ev0, &m->evx, &m->ev1, &m->ev2, &m->evd})
     BTA_CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
   BTA_CUDA_TRY(cudaDeviceSynchronize());
   return BTA_OK;
@@ -525,21 +561,33 @@ bta_status inla_value_and_grad(inla_model* m, const double* theta, int32_t batch
   for (int i = 0; i < batch; ++i)
     if (!finite_theta(theta + (size_t)i * m->d, m->d)) return BTA_ERR_ARG;
   const int use_graph = opts ? opts->use_graph : 1;
-  const int g = grad ? 1 : 0;
-  for (int i = 0; i < batch; ++i) {
-    bta_status st = run_eval(m, theta + (size_t)i * m->d, g, use_graph, stream);
-    f[i] = m->last[0];
-    if (grad)
-      for (int j = 0; j < m->d; ++j) grad[(size_t)i * m->d + j] = m->last[1 + j];
-    if (st != BTA_OK) return st;
+  int group = opts && opts->streams > 1 ? opts->streams : 1;
+  group = std::min(group, std::min<int>(batch, kMaxBatch / 2));
+  BTA_TRY(ensure_ctx(m, group));
+  const int mode = grad ? 1 : 0;
+  const int d = m->d, no = out_size(d);
+  bta_status st = BTA_OK;
+  for (int i0 = 0; i0 < batch; i0 += group) {
+    const int cnt = std::min(group, batch - i0);
+    std::memcpy(m->htheta, theta + (size_t)i0 * d, (size_t)cnt * d * sizeof(double));
+    bta_status s1 = run_group(m, mode, cnt, use_graph, stream);
+    if (s1 != BTA_OK && s1 != BTA_ERR_NOT_SPD) return s1;
+    if (s1 != BTA_OK) st = s1;
+    for (int e = 0; e < cnt; ++e) {
+      const double* o = m->hout + (size_t)e * no;
+      f[i0 + e] = o[0];
+      if (grad)
+        for (int j = 0; j < d; ++j) grad[(size_t)(i0 + e) * d + j] = o[1 + j];
+    }
   }
-  return BTA_OK;
+  return st;
 }
 
 bta_status inla_backward(inla_model* m, double* grad, int32_t use_graph, cudaStream_t stream) {
   if (!m || !grad) return BTA_ERR_ARG;
-  if (!m->have_factors) return BTA_ERR_STATE;
-  bta_status st = run_eval(m, nullptr, 2, use_graph, stream);
+  if (m->ctx.empty() || !m->ctx[0].have_factors) return BTA_ERR_STATE;
+  for (size_t e = 1; e < m->ctx.size(); ++e) m->ctx[e].have_factors = 0;
+  bta_status st = run_group(m, 2, 1, use_graph, stream);
   for (int j = 0; j < m->d; ++j) grad[j] = m->last[1 + j];
   return st;
 }
@@ -568,7 +616,8 @@ bta_status inla_last_parts(const inla_model* m, double* parts, double* phases) {
 
 bta_status inla_copy_mode(const inla_model* m, double* dst, cudaStream_t stream) {
   if (!m || !dst) return BTA_ERR_ARG;
-  BTA_CUDA_TRY(cudaMemcpyAsync(dst, m->x, ((size_t)m->n * m->ld + m->a) * sizeof(double),
+  if (m->ctx.empty()) return BTA_ERR_STATE;
+  BTA_CUDA_TRY(cudaMemcpyAsync(dst, m->ctx[0].x, ((size_t)m->n * m->ld + m->a) * sizeof(double),
                                cudaMemcpyDeviceToDevice, stream));
   return BTA_OK;
 }

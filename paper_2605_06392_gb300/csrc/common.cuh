@@ -3,6 +3,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <utility>
 #include <cuda_runtime.h>
 
 #include "../../include/bta.h"
@@ -44,6 +45,35 @@ extern int64_t g_launches;
     }                                                                         \
   } while (0)
 
+// Launch priority for the kernels on the sweeps' critical path (the
+// diagonal-block factorisation): while set (PriorityScope), launches carry
+// the device's highest stream priority as a launch attribute, so the
+// scheduler places them ahead of the wide products of a concurrent sweep.
+extern int g_launch_priority;   // 0: default priority
+struct PriorityScope {
+  int saved;
+  explicit PriorityScope(int prio) : saved(g_launch_priority) { g_launch_priority = prio; }
+  ~PriorityScope() { g_launch_priority = saved; }
+};
+int highest_priority();
+
+// Launch a kernel with the current launch priority (cudaLaunchKernelEx).
+template <class... KArgs, class... Args>
+cudaError_t launch_prio(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s,
+                        Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributePriority;
+  attr[0].val.priority = g_launch_priority;
+  cfg.attrs = attr;
+  cfg.numAttrs = g_launch_priority ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 inline int pad_ld(int b) { return (b + kPad - 1) / kPad * kPad; }
 inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
@@ -55,6 +85,9 @@ inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 // ----------------------------------------------------------------------------
 enum Tri : int { TRI_NONE = 0, TRI_LOWER = 1, TRI_UPPER = 2 };
 
+// Problems per batched launch (pointer arrays travel in the kernel parameters).
+constexpr int kMaxBatch = 32;
+
 struct Gemm {
   int M = 0, N = 0, K = 0;
   const double* A = nullptr; int lda = 0; int transA = 0; int triA = TRI_NONE;
@@ -63,13 +96,19 @@ struct Gemm {
   const double* Cin = nullptr; int ldcin = 0;   // may alias C; ignored when beta == 0
   double alpha = 1.0, beta = 0.0;
   int out_lower = 0;   // write only C[i][j] with i >= j (tiles above the diagonal skipped)
-  // batched: blockIdx.z selects problem z, pointers advance by these strides
+  // Batched: `batch` problems of the same shape; when batch > 1 the pointers
+  // come from these host arrays (Cinb may be null: Cin = C) and A..Cin are
+  // ignored.  Larger batches are split into launches of kMaxBatch.
   int batch = 1;
-  int64_t strideA = 0, strideB = 0, strideC = 0, strideCin = 0;
+  const double* const* Ab = nullptr;
+  const double* const* Bb = nullptr;
+  double* const* Cb = nullptr;
+  const double* const* Cinb = nullptr;
 };
 bta_status gemm_f64(const Gemm& g, cudaStream_t s);
 
 // y[M] = alpha * op(A) x + beta * yin ; A column-major lda; tri masks A.
+// Batched like Gemm: per-problem A, x, y, yin and GEMV work areas.
 struct Gemv {
   int M = 0, K = 0;
   const double* A = nullptr; int lda = 0; int transA = 0; int triA = TRI_NONE;
@@ -77,6 +116,12 @@ struct Gemv {
   double* y = nullptr;
   const double* yin = nullptr;    // may alias y
   double alpha = 1.0, beta = 0.0;
+  int batch = 1;
+  const double* const* Ab = nullptr;
+  const double* const* xb = nullptr;
+  double* const* yb = nullptr;
+  const double* const* yinb = nullptr;   // null: yin = y
+  double* const* workb = nullptr;
 };
 bta_status gemv_f64(const Gemv& g, double* work, cudaStream_t s);
 constexpr int kGemvSplit = 16;      // K splits; work needs kGemvSplit * M doubles
@@ -90,11 +135,18 @@ constexpr int kGemvSplit = 16;      // K splits; work needs kGemvSplit * M doubl
 // ----------------------------------------------------------------------------
 bta_status potrf_inv(double* A, int n, int ld, double* scratch, double* logdet_parts,
                      int32_t* fail, int32_t fail_code, cudaStream_t s);
+// The same on `count` blocks of one size at once (host arrays of per-block
+// pointers and failure codes).
+bta_status potrf_inv_batch(int count, double* const* A, int n, int ld, double* const* scratch,
+                           double* const* logdet_parts, int32_t* const* fail,
+                           const int32_t* fail_code, cudaStream_t s);
 int potrf_inv_slots(int n);   // number of logdet slots potrf_inv writes
 
 // Small helpers (sweep.cu)
 bta_status copy_block(const double* src, int lds, double* dst, int ldd, int rows, int cols,
                       double alpha, int mode, cudaStream_t s);  // mode 0 copy, 1 mirror lower->full
+bta_status copy_block_batch(int count, const double* const* src, int lds, double* const* dst,
+                            int ldd, int rows, int cols, double alpha, int mode, cudaStream_t s);
 bta_status fill_value(double* p, int64_t n, double v, cudaStream_t s);
 bta_status sum_slots(const double* parts, int nparts, double* out, int accumulate,
                      cudaStream_t s);

@@ -14,21 +14,32 @@
 namespace bta {
 
 int64_t g_launches = 0;
+int g_launch_priority = 0;
+
+int highest_priority() {
+  int least = 0, greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) return 0;
+  return greatest;
+}
 
 namespace {
 
 constexpr int BK = 16;
 constexpr int NT = 256;
 
+// Kernel parameters: shared shape and flags, per-problem pointers indexed by
+// blockIdx.z (a batch of same-shaped products in one launch).
 struct GemmDev {
   int M, N, K;
-  const double* A; int lda, transA, triA;
-  const double* B; int ldb, transB, triB;
-  double* C; int ldc;
-  const double* Cin; int ldcin;
+  int lda, transA, triA;
+  int ldb, transB, triB;
+  int ldc, ldcin;
   double alpha, beta;
   int out_lower;
-  int64_t strideA, strideB, strideC, strideCin;
+  const double* A[kMaxBatch];
+  const double* B[kMaxBatch];
+  double* C[kMaxBatch];
+  const double* Cin[kMaxBatch];
 };
 
 __device__ __forceinline__ bool a_zero(int tri, int m, int k) {
@@ -49,10 +60,10 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(GemmDev g) {
 
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
   if (g.out_lower && n0 > m0 + BM - 1) return;
-  const double* A = g.A + (int64_t)blockIdx.z * g.strideA;
-  const double* B = g.B + (int64_t)blockIdx.z * g.strideB;
-  double* C = g.C + (int64_t)blockIdx.z * g.strideC;
-  const double* Cin = g.Cin ? g.Cin + (int64_t)blockIdx.z * g.strideCin : nullptr;
+  const double* __restrict__ A = g.A[blockIdx.z];
+  const double* __restrict__ B = g.B[blockIdx.z];
+  double* C = g.C[blockIdx.z];
+  const double* Cin = g.Cin[blockIdx.z];
 
   // K range that can hold nonzeros for this tile.
   int kbeg = 0, kend = g.K;
@@ -153,59 +164,73 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(GemmDev g) {
 // ----------------------------------------------------------------------------
 // GEMV with a deterministic split over K.
 // ----------------------------------------------------------------------------
-__global__ void gemv_n_partial(int M, int K, const double* __restrict__ A, int lda, int triA,
-                               const double* __restrict__ x, double* __restrict__ part) {
+struct GemvDev {
+  int M, K, lda, triA, nsplit;
+  double alpha, beta;
+  const double* A[kMaxBatch];
+  const double* x[kMaxBatch];
+  double* y[kMaxBatch];
+  const double* yin[kMaxBatch];
+  double* work[kMaxBatch];
+};
+
+// y = op(A) x with op(A) = A: thread per output row, partial sums over a K
+// split written to a fixed slot (summed in order by gemv_finish).
+__global__ void gemv_n_partial(GemvDev g) {
+  const int z = blockIdx.z;
+  const double* __restrict__ A = g.A[z];
+  const double* __restrict__ x = g.x[z];
   int m = blockIdx.x * blockDim.x + threadIdx.x;
   int split = blockIdx.y;
-  int kc = (K + gridDim.y - 1) / gridDim.y;
-  int kb = split * kc, ke = min(K, kb + kc);
-  if (triA == TRI_LOWER) ke = min(ke, m + 1);
-  if (triA == TRI_UPPER) kb = max(kb, m);
+  int kc = (g.K + gridDim.y - 1) / gridDim.y;
+  int kb = split * kc, ke = min(g.K, kb + kc);
+  if (g.triA == TRI_LOWER) ke = min(ke, m + 1);
+  if (g.triA == TRI_UPPER) kb = max(kb, m);
   double s = 0.0;
-  if (m < M)
-    for (int k = kb; k < ke; ++k) s = fma(A[m + (int64_t)k * lda], x[k], s);
-  if (m < M) part[(int64_t)split * M + m] = s;
+  if (m < g.M)
+    for (int k = kb; k < ke; ++k) s = fma(A[m + (int64_t)k * g.lda], x[k], s);
+  if (m < g.M) g.work[z][(int64_t)split * g.M + m] = s;
 }
 
 // y[m] = sum_k A[k, m] x[k] (op(A) = A^T), one warp per output, lanes over K.
-__global__ void gemv_t_partial(int M, int K, const double* __restrict__ A, int lda, int triA,
-                               const double* __restrict__ x, double* __restrict__ part) {
-  int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+__global__ void gemv_t_partial(GemvDev g) {
+  const int z = blockIdx.z;
+  const double* __restrict__ A = g.A[z];
+  const double* __restrict__ x = g.x[z];
+  int m = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   int split = blockIdx.y;
-  int m = warp;
-  if (m >= M) return;
-  int kc = (K + gridDim.y - 1) / gridDim.y;
-  int kb = split * kc, ke = min(K, kb + kc);
+  if (m >= g.M) return;
+  int kc = (g.K + gridDim.y - 1) / gridDim.y;
+  int kb = split * kc, ke = min(g.K, kb + kc);
   // op(A)[m,k] = A[k,m]; op(A) lower -> zero for k > m
-  if (triA == TRI_LOWER) ke = min(ke, m + 1);
-  if (triA == TRI_UPPER) kb = max(kb, m);
+  if (g.triA == TRI_LOWER) ke = min(ke, m + 1);
+  if (g.triA == TRI_UPPER) kb = max(kb, m);
   double s = 0.0;
-  for (int k = kb + lane; k < ke; k += 32) s = fma(A[k + (int64_t)m * lda], x[k], s);
+  for (int k = kb + lane; k < ke; k += 32) s = fma(A[k + (int64_t)m * g.lda], x[k], s);
 #pragma unroll
   for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) part[(int64_t)split * M + m] = s;
+  if (lane == 0) g.work[z][(int64_t)split * g.M + m] = s;
 }
 
-__global__ void gemv_finish(int M, int nsplit, const double* __restrict__ part, double alpha,
-                            double beta, const double* yin, double* y) {
+__global__ void gemv_finish(GemvDev g) {
+  const int z = blockIdx.y;
   int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= M) return;
+  if (m >= g.M) return;
+  const double* part = g.work[z];
   double s = 0.0;
-  for (int j = 0; j < nsplit; ++j) s += part[(int64_t)j * M + m];
-  double v = alpha * s;
-  if (beta != 0.0) v = fma(beta, yin[m], v);
-  y[m] = v;
+  for (int j = 0; j < g.nsplit; ++j) s += part[(int64_t)j * g.M + m];
+  double v = g.alpha * s;
+  if (g.beta != 0.0) v = fma(g.beta, g.yin[z][m], v);
+  g.y[z][m] = v;
 }
 
 }  // namespace
 
 bta_status gemm_f64(const Gemm& g, cudaStream_t s) {
-  if (g.M <= 0 || g.N <= 0) return BTA_OK;
-  GemmDev d{g.M, g.N, g.K, g.A, g.lda, g.transA, g.triA, g.B, g.ldb, g.transB, g.triB,
-            g.C, g.ldc, g.Cin ? g.Cin : g.C, g.Cin ? g.ldcin : g.ldc, g.alpha, g.beta,
-            g.out_lower, g.strideA, g.strideB, g.strideC, g.strideCin};
-  if (g.K <= 0) { d.K = 0; }
+  if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return BTA_OK;
+  if (g.Ab ? !(g.Bb && g.Cb) : (g.batch != 1 || !g.A || !g.B || !g.C)) return BTA_ERR_ARG;
+  const int nb = g.batch;
   // Tile choice.  Every tile is FP64-pipe bound and the hardware spreads
   // tiles evenly over the 152 SMs, so an op takes about
   // ceil(tiles / 152) x (BM x BN x K) / rate: pick the shape minimising that
@@ -219,7 +244,7 @@ bta_status gemm_f64(const Gemm& g, cudaStream_t s) {
     } else {
       for (int r = 0; r < tm; ++r) u += std::min(tn, (r * bm + bm - 1) / bn + 1);
     }
-    return u * g.batch;
+    return u * nb;
   };
   auto cost = [&](int t, double pen) {
     const int64_t u = units(t, t);
@@ -233,38 +258,73 @@ bta_status gemm_f64(const Gemm& g, cudaStream_t s) {
     if (c32 < best) { bm = 32; best = c32; }
     if (c16 < best) { bm = 16; best = c16; }
   }
-  if (bm == 0) {
-    dim3 grid(cdiv(g.M, 16), cdiv(g.N, 64), g.batch);
-    gemm_f64_kernel<16, 64><<<grid, NT, 0, s>>>(d);
-  } else if (bm == 64) {
-    dim3 grid(cdiv(g.M, 64), cdiv(g.N, 64), g.batch);
-    gemm_f64_kernel<64, 64><<<grid, NT, 0, s>>>(d);
-  } else if (bm == 32) {
-    dim3 grid(cdiv(g.M, 32), cdiv(g.N, 32), g.batch);
-    gemm_f64_kernel<32, 32><<<grid, NT, 0, s>>>(d);
-  } else {
-    dim3 grid(cdiv(g.M, 16), cdiv(g.N, 16), g.batch);
-    gemm_f64_kernel<16, 16><<<grid, NT, 0, s>>>(d);
+  GemmDev d;
+  d.M = g.M; d.N = g.N; d.K = g.K > 0 ? g.K : 0;
+  d.lda = g.lda; d.transA = g.transA; d.triA = g.triA;
+  d.ldb = g.ldb; d.transB = g.transB; d.triB = g.triB;
+  d.ldc = g.ldc; d.ldcin = g.Cin || g.Cinb ? g.ldcin : g.ldc;
+  d.alpha = g.alpha; d.beta = g.beta; d.out_lower = g.out_lower;
+  for (int z0 = 0; z0 < nb; z0 += kMaxBatch) {
+    const int cnt = std::min(kMaxBatch, nb - z0);
+    for (int z = 0; z < cnt; ++z) {
+      if (!g.Ab) {   // single problem given by the scalar pointers
+        d.A[z] = g.A; d.B[z] = g.B; d.C[z] = g.C; d.Cin[z] = g.Cin ? g.Cin : g.C;
+      } else {
+        d.A[z] = g.Ab[z0 + z]; d.B[z] = g.Bb[z0 + z]; d.C[z] = g.Cb[z0 + z];
+        d.Cin[z] = g.Cinb ? g.Cinb[z0 + z] : g.Cb[z0 + z];
+      }
+    }
+    if (bm == 0) {
+      dim3 grid(cdiv(g.M, 16), cdiv(g.N, 64), cnt);
+      launch_prio(gemm_f64_kernel<16, 64>, grid, dim3(NT), s, d);
+    } else if (bm == 64) {
+      dim3 grid(cdiv(g.M, 64), cdiv(g.N, 64), cnt);
+      launch_prio(gemm_f64_kernel<64, 64>, grid, dim3(NT), s, d);
+    } else if (bm == 32) {
+      dim3 grid(cdiv(g.M, 32), cdiv(g.N, 32), cnt);
+      launch_prio(gemm_f64_kernel<32, 32>, grid, dim3(NT), s, d);
+    } else {
+      dim3 grid(cdiv(g.M, 16), cdiv(g.N, 16), cnt);
+      launch_prio(gemm_f64_kernel<16, 16>, grid, dim3(NT), s, d);
+    }
+    BTA_LAUNCHED();
   }
-  BTA_LAUNCHED();
   return BTA_OK;
 }
 
 bta_status gemv_f64(const Gemv& g, double* work, cudaStream_t s) {
-  if (g.M <= 0) return BTA_OK;
+  if (g.M <= 0 || g.batch <= 0) return BTA_OK;
+  if (g.Ab ? !(g.xb && g.yb && g.workb) : (g.batch != 1 || !g.A || !g.x || !g.y || !work))
+    return BTA_ERR_ARG;
+  const int nb = g.batch;
   int nsplit = g.K >= 512 ? kGemvSplit : 1;
   if (g.K <= 0) nsplit = 1;
-  if (!g.transA) {
-    dim3 grid(cdiv(g.M, 128), nsplit);
-    gemv_n_partial<<<grid, 128, 0, s>>>(g.M, g.K, g.A, g.lda, g.triA, g.x, work);
-  } else {
-    dim3 grid(cdiv((int64_t)g.M * 32, 256), nsplit);
-    gemv_t_partial<<<grid, 256, 0, s>>>(g.M, g.K, g.A, g.lda, g.triA, g.x, work);
+  GemvDev d;
+  d.M = g.M; d.K = g.K > 0 ? g.K : 0; d.lda = g.lda; d.triA = g.triA; d.nsplit = nsplit;
+  d.alpha = g.alpha; d.beta = g.beta;
+  for (int z0 = 0; z0 < nb; z0 += kMaxBatch) {
+    const int cnt = std::min(kMaxBatch, nb - z0);
+    for (int z = 0; z < cnt; ++z) {
+      if (!g.Ab) {   // single problem given by the scalar pointers
+        d.A[z] = g.A; d.x[z] = g.x; d.y[z] = g.y; d.yin[z] = g.yin ? g.yin : g.y;
+        d.work[z] = work;
+      } else {
+        d.A[z] = g.Ab[z0 + z]; d.x[z] = g.xb[z0 + z]; d.y[z] = g.yb[z0 + z];
+        d.yin[z] = g.yinb ? g.yinb[z0 + z] : g.yb[z0 + z];
+        d.work[z] = g.workb[z0 + z];
+      }
+    }
+    if (!g.transA) {
+      dim3 grid(cdiv(g.M, 128), nsplit, cnt);
+      gemv_n_partial<<<grid, 128, 0, s>>>(d);
+    } else {
+      dim3 grid(cdiv((int64_t)g.M * 32, 256), nsplit, cnt);
+      gemv_t_partial<<<grid, 256, 0, s>>>(d);
+    }
+    BTA_LAUNCHED();
+    gemv_finish<<<dim3(cdiv(g.M, 256), cnt), 256, 0, s>>>(d);
+    BTA_LAUNCHED();
   }
-  BTA_LAUNCHED();
-  gemv_finish<<<cdiv(g.M, 256), 256, 0, s>>>(g.M, nsplit, work, g.alpha, g.beta,
-                                               g.yin ? g.yin : g.y, g.y);
-  BTA_LAUNCHED();
   return BTA_OK;
 }
 

@@ -74,6 +74,9 @@ bta_status launch_arrow_dot(const ModelDev& md, const double* ZC, int t, double*
 // Stencil quadratic forms x_t^(p)T S x_u^(q).  out: [k*k][chunks][kNP]
 bta_status launch_pattern_quad(const ModelDev& md, const double* xr, const double* xc,
                                double* out, cudaStream_t s);
+// All of them for one mode x: QD[t] = x_t x_t forms, QB[t] = x_{t+1} x_t forms.
+bta_status launch_pattern_quad_all(const ModelDev& md, const double* x, double* QD, double* QB,
+                                  cudaStream_t s);
 // Squared residuals per response.  out: [k][rchunks]
 int resid_chunks(const ModelDev& md);
 bta_status launch_residual(const ModelDev& md, const double* x, double* out, cudaStream_t s);

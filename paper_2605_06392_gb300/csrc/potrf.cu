@@ -25,21 +25,38 @@ constexpr int T = kPad;   // leaf size
 
 // 32 x 32 leaf: A = L1 D L1^T (unit-lower L1) by right-looking elimination,
 // with the inverse X = L1^{-1} built in the same steps (Gauss-Jordan on the
-// unit factor), then L^{-1} = D^{-1/2} X and log|A| = sum log D_j.  Step j
-// reads only column j of the trailing matrix and row j of X, both final at
-// the end of step j-1, and writes only positions right of column j or below
-// row j, so one barrier per step suffices.  Each of the 128 threads owns a
-// fixed set of lower-triangle positions (i, k) and updates each of them once
-// per step while i > j: the trailing matrix if k > j, X if k <= j.
+// unit factor), then L^{-1} = D^{-1/2} X and log|A| = sum log D_j.
+//
+// On GB300 every warp-wide FP64 instruction occupies its SM sub-partition's
+// FP64 pipe for ~64 cycles, so the leaf is written to issue as few FP64
+// instructions as possible on its serial chain: per step j,
+//   (a) warp 0 scales column j once, l_ij = S_ij / D_j (one multiply per row,
+//       with 1 / D_j computed once, by the thread that last updated D_j);
+//   (b) every owned lower-triangle position (i, k), i > j, does one FMA:
+//       the trailing matrix if k > j (S_ik -= l_ij S_kj), X otherwise
+//       (X_ik -= l_ij X_jk).
+// Step j reads only column j / row j, final after step j-1, so two
+// barriers per step suffice.
 constexpr int kLeafThreads = 128;
 constexpr int kLeafPos = T * (T + 1) / 2;
 constexpr int kLeafPer = (kLeafPos + kLeafThreads - 1) / kLeafThreads;
 
-__global__ void __launch_bounds__(kLeafThreads) potrf_inv_leaf(double* A, int ld,
-                                                               double* logdet_slot, int32_t* fail,
-                                                               int32_t fail_code) {
+struct LeafDev {
+  int ld;
+  double* A[kMaxBatch];
+  double* slot[kMaxBatch];
+  int32_t* fail[kMaxBatch];
+  int32_t code[kMaxBatch];
+};
+
+// One CTA per block of the batch (blockIdx.x).
+__global__ void __launch_bounds__(kLeafThreads) potrf_inv_leaf(LeafDev dv) {
+  double* A = dv.A[blockIdx.x];
+  const int ld = dv.ld;
   __shared__ double S[T][T + 1];
   __shared__ double X[T][T + 1];
+  __shared__ double lcol[T];
+  __shared__ double rinv[T];   // 1 / D_j
   const int tid = threadIdx.x;
   int pi[kLeafPer], pk[kLeafPer];
 #pragma unroll
@@ -61,23 +78,33 @@ __global__ void __launch_bounds__(kLeafThreads) potrf_inv_leaf(double* A, int ld
     X[i][j] = (i == j) ? 1.0 : 0.0;
   }
   __syncthreads();
+  if (tid == 0) rinv[0] = 1.0 / S[0][0];
+  __syncthreads();
   for (int j = 0; j < T; ++j) {
-    const double invd = 1.0 / S[j][j];
+    if (tid > j && tid < T) lcol[tid] = S[tid][j] * rinv[j];
+    __syncthreads();
 #pragma unroll
     for (int r = 0; r < kLeafPer; ++r) {
       const int i = pi[r], k = pk[r];
       if (i > j) {
-        const double lij = S[i][j] * invd;
-        if (k > j) S[i][k] = fma(-lij, S[k][j], S[i][k]);
-        else X[i][k] = fma(-lij, X[j][k], X[i][k]);
+        const double lij = lcol[i];
+        if (k > j) {
+          const double v = fma(-lij, S[k][j], S[i][k]);
+          S[i][k] = v;
+          if (i == j + 1 && k == j + 1) rinv[j + 1] = 1.0 / v;   // D_{j+1} is final now
+        } else {
+          X[i][k] = fma(-lij, X[j][k], X[i][k]);
+        }
       }
     }
     __syncthreads();
   }
+  if (tid < T) rinv[tid] = 1.0 / sqrt(S[tid][tid]);
+  __syncthreads();
 #pragma unroll
   for (int r = 0; r < kLeafPer; ++r) {
     const int i = pi[r], k = pk[r];
-    if (i >= 0) A[i + (int64_t)k * ld] = X[i][k] / sqrt(S[i][i]);
+    if (i >= 0) A[i + (int64_t)k * ld] = X[i][k] * rinv[i];
   }
   if (tid < 32) {
     const double dj = S[tid][tid];
@@ -87,56 +114,93 @@ __global__ void __launch_bounds__(kLeafThreads) potrf_inv_leaf(double* A, int ld
     for (int o = 16; o; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
     const unsigned anybad = __ballot_sync(0xffffffffu, bad);
     if (tid == 0) {
-      *logdet_slot = l;
-      if (anybad) atomicCAS(fail, -1, fail_code);
+      *dv.slot[blockIdx.x] = l;
+      if (anybad) atomicCAS(dv.fail[blockIdx.x], -1, dv.code[blockIdx.x]);
     }
   }
 }
 
-bta_status rec(double* A, int n, int ld, double* scratch, double* slots, int32_t* fail,
-               int32_t fail_code, cudaStream_t s) {
+// A batch of same-sized diagonal blocks factored together: every step of
+// the recursion is one launch over all of them.
+struct PB {
+  int cnt;
+  double* A[kMaxBatch];
+  double* W[kMaxBatch];
+  double* slots[kMaxBatch];
+  int32_t* fail[kMaxBatch];
+  int32_t code[kMaxBatch];
+};
+
+bta_status rec(const PB& b, int64_t aoff, int n, int ld, int64_t woff, int soff,
+               cudaStream_t s) {
+  const int cnt = b.cnt;
   if (n == T) {
-    potrf_inv_leaf<<<1, kLeafThreads, 0, s>>>(A, ld, slots, fail, fail_code);
+    LeafDev dv;
+    dv.ld = ld;
+    for (int z = 0; z < cnt; ++z) {
+      dv.A[z] = b.A[z] + aoff;
+      dv.slot[z] = b.slots[z] + soff;
+      dv.fail[z] = b.fail[z];
+      dv.code[z] = b.code[z];
+    }
+    launch_prio(potrf_inv_leaf, dim3(cnt), dim3(kLeafThreads), s, dv);
     BTA_LAUNCHED();
     return BTA_OK;
   }
-  int p = n / T;
-  int n1 = (p / 2) * T, n2 = n - n1;
-  double* A11 = A;
-  double* A21 = A + n1;
-  double* A22 = A + n1 + (int64_t)n1 * ld;
-  double* W1 = scratch;                       // n2 x n1, ld n2 : L21
-  double* W2 = scratch + (int64_t)n2 * n1;    // n2 x n1        : L21 L11^{-1}
-  double* sub = W2 + (int64_t)n2 * n1;        // scratch for the recursion on A22
-  BTA_TRY(rec(A11, n1, ld, sub, slots, fail, fail_code, s));
+  const int p = n / T;
+  const int n1 = (p / 2) * T, n2 = n - n1;
+  const int64_t o11 = aoff, o21 = aoff + n1, o22 = aoff + n1 + (int64_t)n1 * ld;
+  const int64_t w1 = woff, w2 = woff + (int64_t)n2 * n1;   // L21, L21 L11^{-1}
+  const int64_t wsub = w2 + (int64_t)n2 * n1;              // scratch of the recursion
+  const double* A11[kMaxBatch];
+  const double* A21c[kMaxBatch];
+  const double* A22c[kMaxBatch];
+  double* A21[kMaxBatch];
+  double* A22[kMaxBatch];
+  double* W1[kMaxBatch];
+  double* W2[kMaxBatch];
+  const double* W1c[kMaxBatch];
+  const double* W2c[kMaxBatch];
+  for (int z = 0; z < cnt; ++z) {
+    A11[z] = b.A[z] + o11;
+    A21[z] = b.A[z] + o21;
+    A21c[z] = A21[z];
+    A22[z] = b.A[z] + o22;
+    A22c[z] = A22[z];
+    W1[z] = b.W[z] + w1;
+    W2[z] = b.W[z] + w2;
+    W1c[z] = W1[z];
+    W2c[z] = W2[z];
+  }
+  BTA_TRY(rec(b, o11, n1, ld, wsub, soff, s));
   {  // L21 = A21 * (L11^{-1})^T
-    Gemm g; g.M = n2; g.N = n1; g.K = n1;
-    g.A = A21; g.lda = ld;
-    g.B = A11; g.ldb = ld; g.transB = 1; g.triB = TRI_UPPER;   // (lower W)^T is upper
-    g.C = W1; g.ldc = n2;
+    Gemm g; g.M = n2; g.N = n1; g.K = n1; g.batch = cnt;
+    g.Ab = A21c; g.lda = ld;
+    g.Bb = A11; g.ldb = ld; g.transB = 1; g.triB = TRI_UPPER;   // (lower W)^T is upper
+    g.Cb = W1; g.ldc = n2;
     BTA_TRY(gemm_f64(g, s));
   }
   {  // A22 -= L21 L21^T (lower)
-    Gemm g; g.M = n2; g.N = n2; g.K = n1;
-    g.A = W1; g.lda = n2;
-    g.B = W1; g.ldb = n2; g.transB = 1;
-    g.C = A22; g.ldc = ld; g.Cin = A22; g.ldcin = ld;
+    Gemm g; g.M = n2; g.N = n2; g.K = n1; g.batch = cnt;
+    g.Ab = W1c; g.lda = n2;
+    g.Bb = W1c; g.ldb = n2; g.transB = 1;
+    g.Cb = A22; g.ldc = ld; g.Cinb = A22c; g.ldcin = ld;
     g.alpha = -1.0; g.beta = 1.0; g.out_lower = 1;
     BTA_TRY(gemm_f64(g, s));
   }
-  BTA_TRY(rec(A22, n2, ld, sub, slots + n1 / T, fail, fail_code, s));
+  BTA_TRY(rec(b, o22, n2, ld, wsub, soff + n1 / T, s));
   {  // W2 = L21 * L11^{-1}
-    Gemm g; g.M = n2; g.N = n1; g.K = n1;
-    g.A = W1; g.lda = n2;
-    g.B = A11; g.ldb = ld; g.triB = TRI_LOWER;
-    g.C = W2; g.ldc = n2;
+    Gemm g; g.M = n2; g.N = n1; g.K = n1; g.batch = cnt;
+    g.Ab = W1c; g.lda = n2;
+    g.Bb = A11; g.ldb = ld; g.triB = TRI_LOWER;
+    g.Cb = W2; g.ldc = n2;
     BTA_TRY(gemm_f64(g, s));
   }
   {  // (L^{-1})21 = -L22^{-1} W2
-    Gemm g; g.M = n2; g.N = n1; g.K = n2;
-    g.A = A22; g.lda = ld; g.triA = TRI_LOWER;
-    g.B = W2; g.ldb = n2;
-    g.C = A21; g.ldc = ld; g.alpha = -1.0;
+    Gemm g; g.M = n2; g.N = n1; g.K = n2; g.batch = cnt;
+    g.Ab = A22c; g.lda = ld; g.triA = TRI_LOWER;
+    g.Bb = W2c; g.ldb = n2;
+    g.Cb = A21; g.ldc = ld; g.alpha = -1.0;
     BTA_TRY(gemm_f64(g, s));
   }
   return BTA_OK;
@@ -146,10 +210,29 @@ bta_status rec(double* A, int n, int ld, double* scratch, double* slots, int32_t
 
 int potrf_inv_slots(int n) { return n / T; }
 
+bta_status potrf_inv_batch(int count, double* const* A, int n, int ld, double* const* scratch,
+                           double* const* logdet_parts, int32_t* const* fail,
+                           const int32_t* fail_code, cudaStream_t s) {
+  if (n <= 0 || n % T || count < 0) return BTA_ERR_ARG;
+  PriorityScope prio(highest_priority());   // the sweep's critical path
+  for (int z0 = 0; z0 < count; z0 += kMaxBatch) {
+    PB b;
+    b.cnt = count - z0 < kMaxBatch ? count - z0 : kMaxBatch;
+    for (int z = 0; z < b.cnt; ++z) {
+      b.A[z] = A[z0 + z];
+      b.W[z] = scratch[z0 + z];
+      b.slots[z] = logdet_parts[z0 + z];
+      b.fail[z] = fail[z0 + z];
+      b.code[z] = fail_code[z0 + z];
+    }
+    BTA_TRY(rec(b, 0, n, ld, 0, 0, s));
+  }
+  return BTA_OK;
+}
+
 bta_status potrf_inv(double* A, int n, int ld, double* scratch, double* logdet_parts,
                      int32_t* fail, int32_t fail_code, cudaStream_t s) {
-  if (n <= 0 || n % T) return BTA_ERR_ARG;
-  return rec(A, n, ld, scratch, logdet_parts, fail, fail_code, s);
+  return potrf_inv_batch(1, &A, n, ld, &scratch, &logdet_parts, &fail, &fail_code, s);
 }
 
 }  // namespace bta

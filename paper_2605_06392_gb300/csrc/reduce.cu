@@ -83,6 +83,34 @@ __global__ void __launch_bounds__(RT) pattern_quad_kernel(PatArgs a, const doubl
   block_sum<kNP>(v, out + ((int64_t)pq * gridDim.x + chunk) * kNP, 1);
 }
 
+// All stencil quadratic forms of one mode x in one launch: blockIdx.z < n
+// gives x_t^(p)T S x_t^(q) (into QD[t]), blockIdx.z = n + t gives
+// x_{t+1}^(p)T S x_t^(q) (into QB[t]).
+__global__ void __launch_bounds__(RT) pattern_quad_all_kernel(PatArgs a,
+                                                              const double* __restrict__ x,
+                                                              int ld, int n, double* QD,
+                                                              double* QB) {
+  const int chunk = blockIdx.x, pq = blockIdx.y;
+  const int z = blockIdx.z;
+  const bool diag = z < n;
+  const int t = diag ? z : z - n;
+  const double* xc = x + (int64_t)t * ld;
+  const double* xr = diag ? xc : xc + ld;
+  const int p = pq / a.k, q = pq % a.k;
+  const int e = chunk * RT + threadIdx.x;
+  double v[kNP] = {0.0, 0.0, 0.0, 0.0};
+  if (e < a.nnz) {
+    int s2 = a.row_of[e], s1 = a.col[e];
+    double w = xr[p * a.ns + s1] * xc[q * a.ns + s2];
+    v[0] = w * a.val[e];
+    v[1] = w * a.val[a.nnz + e];
+    v[2] = w * a.val[2 * a.nnz + e];
+  }
+  const int64_t per = (int64_t)a.k * a.k * gridDim.x * kNP;
+  double* out = (diag ? QD : QB) + (int64_t)t * per;
+  block_sum<kNP>(v, out + ((int64_t)pq * gridDim.x + chunk) * kNP, 1);
+}
+
 // <Z_C, craw> restricted to variable m: rows m*a_r.., columns m*ns..
 __global__ void __launch_bounds__(RT) arrow_dot_kernel(int ns, int a, int a_r,
                                                        const double* __restrict__ ZC,
@@ -266,6 +294,15 @@ bta_status launch_pattern_quad(const ModelDev& md, const double* xr, const doubl
                                double* out, cudaStream_t s) {
   PatArgs a{md.k, md.ns, md.ld, md.nnz, md.row_of, md.col, md.val, nullptr};
   pattern_quad_kernel<<<dim3(pattern_chunks(md), md.k * md.k), RT, 0, s>>>(a, xr, xc, out);
+  BTA_LAUNCHED();
+  return BTA_OK;
+}
+
+bta_status launch_pattern_quad_all(const ModelDev& md, const double* x, double* QD, double* QB,
+                                  cudaStream_t s) {
+  PatArgs a{md.k, md.ns, md.ld, md.nnz, md.row_of, md.col, md.val, nullptr};
+  pattern_quad_all_kernel<<<dim3(pattern_chunks(md), md.k * md.k, 2 * md.nt - 1), RT, 0, s>>>(
+      a, x, md.ld, md.nt, QD, QB);
   BTA_LAUNCHED();
   return BTA_OK;
 }

@@ -6,6 +6,7 @@
 // diagonal factor is kept as L_Di^{-1} (see potrf.cu).
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "sweep.cuh"
 
@@ -96,6 +97,27 @@ __global__ void copy_kernel(const double* __restrict__ src, int lds, double* __r
   }
 }
 
+struct CopyDev {
+  int lds, ldd, rows, cols, mode;
+  double alpha;
+  const double* src[kMaxBatch];
+  double* dst[kMaxBatch];
+};
+
+__global__ void copy_batch_kernel(CopyDev d) {
+  const double* __restrict__ src = d.src[blockIdx.y];
+  double* __restrict__ dst = d.dst[blockIdx.y];
+  const int64_t n = (int64_t)d.rows * d.cols;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int i = (int)(e % d.rows), j = (int)(e / d.rows);
+    double v;
+    if (d.mode == 1 && i < j) v = src[j + (int64_t)i * d.lds];
+    else v = src[i + (int64_t)j * d.lds];
+    dst[i + (int64_t)j * d.ldd] = d.alpha * v;
+  }
+}
+
 __global__ void fill_kernel(double* p, int64_t n, double v) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
        e += (int64_t)gridDim.x * blockDim.x)
@@ -118,6 +140,25 @@ bta_status copy_block(const double* src, int lds, double* dst, int ldd, int rows
   int grid = (int)std::min<int64_t>(cdiv(n, 256), 4 * 152 * 8);
   copy_kernel<<<grid, 256, 0, s>>>(src, lds, dst, ldd, rows, cols, alpha, mode);
   BTA_LAUNCHED();
+  return BTA_OK;
+}
+
+bta_status copy_block_batch(int count, const double* const* src, int lds, double* const* dst,
+                            int ldd, int rows, int cols, double alpha, int mode, cudaStream_t s) {
+  const int64_t n = (int64_t)rows * cols;
+  if (n <= 0 || count <= 0) return BTA_OK;
+  CopyDev d;
+  d.lds = lds; d.ldd = ldd; d.rows = rows; d.cols = cols; d.mode = mode; d.alpha = alpha;
+  for (int z0 = 0; z0 < count; z0 += kMaxBatch) {
+    const int cnt = std::min(kMaxBatch, count - z0);
+    for (int z = 0; z < cnt; ++z) {
+      d.src[z] = src[z0 + z];
+      d.dst[z] = dst[z0 + z];
+    }
+    int gx = (int)std::min<int64_t>(cdiv(n, 256), std::max(1, 4 * 152 * 8 / cnt));
+    copy_batch_kernel<<<dim3(gx, cnt), 256, 0, s>>>(d);
+    BTA_LAUNCHED();
+  }
   return BTA_OK;
 }
 
@@ -155,87 +196,194 @@ void SweepWs::carve(double* base, int ld, int a) {
 
 int logdet_slots(int n, int ld) { return n * potrf_inv_slots(ld) + 1; }
 
+
+namespace {
+
+// Index groups of a set: all items, items with an arrow (grouped by a),
+// items with a vector.
+struct Groups {
+  std::vector<int> all;
+  std::vector<std::vector<int>> arrow;   // one group per distinct a > 0
+  std::vector<int> vec;
+};
+
+Groups make_groups(const SweepItem* it, int m) {
+  Groups g;
+  for (int z = 0; z < m; ++z) {
+    g.all.push_back(z);
+    if (it[z].vec) g.vec.push_back(z);
+    if (it[z].q.a > 0) {
+      bool placed = false;
+      for (auto& grp : g.arrow)
+        if (it[grp[0]].q.a == it[z].q.a) { grp.push_back(z); placed = true; break; }
+      if (!placed) g.arrow.push_back({z});
+    }
+  }
+  return g;
+}
+
+// Gather per-item pointers for a batched launch.
+template <class F>
+std::vector<double*> ptrs(const std::vector<int>& idx, F f) {
+  std::vector<double*> v;
+  v.reserve(idx.size());
+  for (int z : idx) v.push_back(f(z));
+  return v;
+}
+
+inline const double* const* cp(const std::vector<double*>& v) {
+  return reinterpret_cast<const double* const*>(v.data());
+}
+
+bta_status check_set(const SweepItem* it, int m) {
+  if (m < 1) return BTA_ERR_ARG;
+  for (int z = 0; z < m; ++z) {
+    if (it[z].q.n != it[0].q.n || it[z].q.ld != it[0].q.ld) return BTA_ERR_ARG;
+    if (it[z].q.a > kMaxTip) return BTA_ERR_ARG;
+  }
+  return BTA_OK;
+}
+
+}  // namespace
+
 // ----------------------------------------------------------------------------
-// Algorithm 1
+// Algorithm 1 on a set of matrices
 // ----------------------------------------------------------------------------
-bta_status factor_sweep(const bta_desc& q, double* rhs, double* slots, int32_t* fail,
-                        const SweepWs& ws, cudaStream_t s) {
-  const int n = q.n, ld = q.ld, a = q.a;
+bta_status factor_sweep_multi(const SweepItem* it, int m, cudaStream_t s, cudaEvent_t mark) {
+  BTA_TRY(check_set(it, m));
+  const int n = it[0].q.n, ld = it[0].q.ld;
   const int64_t blk = (int64_t)ld * ld;
   const int p = potrf_inv_slots(ld);
-  if (a > kMaxTip) return BTA_ERR_ARG;
-  if (a > 0 && rhs) BTA_TRY(fill_value(ws.vT, a, 0.0, s));
-  if (a > 0) BTA_TRY(fill_value(slots + (int64_t)n * p, 1, 0.0, s));
-  else BTA_TRY(fill_value(slots + (int64_t)n * p, 1, 0.0, s));
+  const Groups G = make_groups(it, m);
+  const int M = (int)G.all.size();
+  for (int z = 0; z < m; ++z) {
+    if (it[z].q.a > 0 && it[z].vec) BTA_TRY(fill_value(it[z].ws.vT, it[z].q.a, 0.0, s));
+    BTA_TRY(fill_value(it[z].slots + (int64_t)n * p, 1, 0.0, s));
+  }
+  auto D = [&](int z, int i) { return it[z].q.D + i * blk; };
+  auto B = [&](int z, int i) { return it[z].q.B + i * blk; };
+  auto Cb = [&](int z, int i) { return it[z].q.C + (int64_t)i * it[z].q.a * ld; };
   for (int i = 0; i < n; ++i) {
-    double* Di = q.D + i * blk;
-    double* Ci = a > 0 ? q.C + (int64_t)i * a * ld : nullptr;
     if (i > 0) {
-      const double* Bp = q.B + (i - 1) * blk;
       {  // D_i -= S_{i-1} = L_B,i-1 L_B,i-1^T (lower)
-        Gemm g; g.M = ld; g.N = ld; g.K = ld;
-        g.A = Bp; g.lda = ld; g.B = Bp; g.ldb = ld; g.transB = 1;
-        g.C = Di; g.ldc = ld; g.Cin = Di; g.ldcin = ld; g.alpha = -1.0; g.beta = 1.0;
-        g.out_lower = 1;
+        auto Bp = ptrs(G.all, [&](int z) { return B(z, i - 1); });
+        auto Di = ptrs(G.all, [&](int z) { return D(z, i); });
+        Gemm g; g.M = ld; g.N = ld; g.K = ld; g.batch = M;
+        g.Ab = cp(Bp); g.lda = ld; g.Bb = cp(Bp); g.ldb = ld; g.transB = 1;
+        g.Cb = Di.data(); g.ldc = ld; g.Cinb = cp(Di); g.ldcin = ld;
+        g.alpha = -1.0; g.beta = 1.0; g.out_lower = 1;
         BTA_TRY(gemm_f64(g, s));
       }
-      if (a > 0) {  // C_i -= L_C,i-1 L_B,i-1^T
-        Gemm g; g.M = a; g.N = ld; g.K = ld;
-        g.A = q.C + (int64_t)(i - 1) * a * ld; g.lda = a;
-        g.B = Bp; g.ldb = ld; g.transB = 1;
-        g.C = Ci; g.ldc = a; g.Cin = Ci; g.ldcin = a; g.alpha = -1.0; g.beta = 1.0;
+      for (const auto& grp : G.arrow) {  // C_i -= L_C,i-1 L_B,i-1^T
+        const int a = it[grp[0]].q.a;
+        auto Cp = ptrs(grp, [&](int z) { return Cb(z, i - 1); });
+        auto Bp = ptrs(grp, [&](int z) { return B(z, i - 1); });
+        auto Ci = ptrs(grp, [&](int z) { return Cb(z, i); });
+        Gemm g; g.M = a; g.N = ld; g.K = ld; g.batch = (int)grp.size();
+        g.Ab = cp(Cp); g.lda = a; g.Bb = cp(Bp); g.ldb = ld; g.transB = 1;
+        g.Cb = Ci.data(); g.ldc = a; g.Cinb = cp(Ci); g.ldcin = a; g.alpha = -1.0; g.beta = 1.0;
         BTA_TRY(gemm_f64(g, s));
       }
     }
-    // L_Di^{-1} in place, log-det slots
-    BTA_TRY(potrf_inv(Di, ld, ld, ws.pot, slots + (int64_t)i * p, fail, i, s));
-    if (a > 0) {  // L_Ci = C_i L_Di^{-T};  T -= L_Ci L_Ci^T
-      Gemm g; g.M = a; g.N = ld; g.K = ld;
-      g.A = Ci; g.lda = a; g.B = Di; g.ldb = ld; g.transB = 1; g.triB = TRI_UPPER;
-      g.C = ws.Wc1; g.ldc = a;
+    {  // L_Di^{-1} in place, log-det slots
+      auto Di = ptrs(G.all, [&](int z) { return D(z, i); });
+      auto W = ptrs(G.all, [&](int z) { return it[z].ws.pot; });
+      auto sl = ptrs(G.all, [&](int z) { return it[z].slots + (int64_t)i * p; });
+      std::vector<int32_t*> fl;
+      std::vector<int32_t> code(M, i);
+      for (int z : G.all) fl.push_back(it[z].fail);
+      BTA_TRY(potrf_inv_batch(M, Di.data(), ld, ld, W.data(), sl.data(), fl.data(), code.data(),
+                              s));
+      if (i == 0 && mark) BTA_CUDA_TRY(cudaEventRecord(mark, s));
+    }
+    for (const auto& grp : G.arrow) {  // L_Ci = C_i L_Di^{-T};  T -= L_Ci L_Ci^T
+      const int a = it[grp[0]].q.a, c = (int)grp.size();
+      auto Ci = ptrs(grp, [&](int z) { return Cb(z, i); });
+      auto Di = ptrs(grp, [&](int z) { return D(z, i); });
+      auto W = ptrs(grp, [&](int z) { return it[z].ws.Wc1; });
+      auto T = ptrs(grp, [&](int z) { return it[z].q.T; });
+      Gemm g; g.M = a; g.N = ld; g.K = ld; g.batch = c;
+      g.Ab = cp(Ci); g.lda = a; g.Bb = cp(Di); g.ldb = ld; g.transB = 1; g.triB = TRI_UPPER;
+      g.Cb = W.data(); g.ldc = a;
       BTA_TRY(gemm_f64(g, s));
-      BTA_TRY(copy_block(ws.Wc1, a, Ci, a, a, ld, 1.0, 0, s));
-      Gemm h; h.M = a; h.N = a; h.K = ld;
-      h.A = Ci; h.lda = a; h.B = Ci; h.ldb = a; h.transB = 1;
-      h.C = q.T; h.ldc = a; h.Cin = q.T; h.ldcin = a; h.alpha = -1.0; h.beta = 1.0;
+      BTA_TRY(copy_block_batch(c, cp(W), a, Ci.data(), a, a, ld, 1.0, 0, s));
+      Gemm h; h.M = a; h.N = a; h.K = ld; h.batch = c;
+      h.Ab = cp(Ci); h.lda = a; h.Bb = cp(Ci); h.ldb = a; h.transB = 1;
+      h.Cb = T.data(); h.ldc = a; h.Cinb = cp(T); h.ldcin = a; h.alpha = -1.0; h.beta = 1.0;
       BTA_TRY(gemm_f64(h, s));
     }
     if (i < n - 1) {  // L_Bi = B_i L_Di^{-T}
-      double* Bi = q.B + i * blk;
-      Gemm g; g.M = ld; g.N = ld; g.K = ld;
-      g.A = Bi; g.lda = ld; g.B = Di; g.ldb = ld; g.transB = 1; g.triB = TRI_UPPER;
-      g.C = ws.W1; g.ldc = ld;
+      auto Bi = ptrs(G.all, [&](int z) { return B(z, i); });
+      auto Di = ptrs(G.all, [&](int z) { return D(z, i); });
+      auto W = ptrs(G.all, [&](int z) { return it[z].ws.W1; });
+      Gemm g; g.M = ld; g.N = ld; g.K = ld; g.batch = M;
+      g.Ab = cp(Bi); g.lda = ld; g.Bb = cp(Di); g.ldb = ld; g.transB = 1; g.triB = TRI_UPPER;
+      g.Cb = W.data(); g.ldc = ld;
       BTA_TRY(gemm_f64(g, s));
-      BTA_TRY(copy_block(ws.W1, ld, Bi, ld, ld, ld, 1.0, 0, s));
+      BTA_TRY(copy_block_batch(M, cp(W), ld, Bi.data(), ld, ld, ld, 1.0, 0, s));
     }
-    if (rhs) {  // z_i = L_Di^{-1} (r_i - L_B,i-1 z_{i-1});  v_T += L_Ci z_i
-      double* ri = rhs + (int64_t)i * ld;
+    if (!G.vec.empty()) {  // z_i = L_Di^{-1} (r_i - L_B,i-1 z_{i-1});  v_T += L_Ci z_i
+      const int c = (int)G.vec.size();
+      auto ri = ptrs(G.vec, [&](int z) { return it[z].vec + (int64_t)i * ld; });
+      auto gv = ptrs(G.vec, [&](int z) { return it[z].ws.gv; });
       if (i > 0) {
-        Gemv g; g.M = ld; g.K = ld; g.A = q.B + (i - 1) * blk; g.lda = ld;
-        g.x = ri - ld; g.y = ri; g.yin = ri; g.alpha = -1.0; g.beta = 1.0;
-        BTA_TRY(gemv_f64(g, ws.gv, s));
+        auto Bp = ptrs(G.vec, [&](int z) { return B(z, i - 1); });
+        auto rp = ptrs(G.vec, [&](int z) { return it[z].vec + (int64_t)(i - 1) * ld; });
+        Gemv g; g.M = ld; g.K = ld; g.lda = ld; g.alpha = -1.0; g.beta = 1.0; g.batch = c;
+        g.Ab = cp(Bp); g.xb = cp(rp); g.yb = ri.data(); g.yinb = cp(ri); g.workb = gv.data();
+        BTA_TRY(gemv_f64(g, nullptr, s));
       }
-      Gemv g; g.M = ld; g.K = ld; g.A = Di; g.lda = ld; g.triA = TRI_LOWER;
-      g.x = ri; g.y = ri;
-      BTA_TRY(gemv_f64(g, ws.gv, s));
-      if (a > 0) {
-        Gemv h; h.M = a; h.K = ld; h.A = Ci; h.lda = a; h.x = ri; h.y = ws.vT; h.yin = ws.vT;
-        h.beta = 1.0;
-        BTA_TRY(gemv_f64(h, ws.gv, s));
+      auto Di = ptrs(G.vec, [&](int z) { return D(z, i); });
+      Gemv g; g.M = ld; g.K = ld; g.lda = ld; g.triA = TRI_LOWER; g.batch = c;
+      g.Ab = cp(Di); g.xb = cp(ri); g.yb = ri.data(); g.workb = gv.data();
+      BTA_TRY(gemv_f64(g, nullptr, s));
+      for (int z : G.vec) {
+        if (it[z].q.a == 0) continue;
+        Gemv h; h.M = it[z].q.a; h.K = ld; h.A = Cb(z, i); h.lda = it[z].q.a;
+        h.x = it[z].vec + (int64_t)i * ld; h.y = it[z].ws.vT; h.yin = it[z].ws.vT; h.beta = 1.0;
+        BTA_TRY(gemv_f64(h, it[z].ws.gv, s));
       }
     }
   }
-  if (a > 0) {
-    tip_kernel<<<1, 32, 0, s>>>(0, a, q.T, rhs ? rhs + (int64_t)n * ld : nullptr, ws.vT,
-                                slots + (int64_t)n * p, fail, n);
+  for (int z = 0; z < m; ++z) {
+    const int a = it[z].q.a;
+    if (a == 0) continue;
+    tip_kernel<<<1, 32, 0, s>>>(0, a, it[z].q.T, it[z].vec ? it[z].vec + (int64_t)n * ld : nullptr,
+                                it[z].ws.vT, it[z].slots + (int64_t)n * p, it[z].fail, n);
     BTA_LAUNCHED();
   }
   return BTA_OK;
 }
 
+bta_status factor_sweep(const bta_desc& q, double* rhs, double* slots, int32_t* fail,
+                        const SweepWs& ws, cudaStream_t s) {
+  SweepItem item;
+  item.q = q; item.vec = rhs; item.slots = slots; item.fail = fail; item.ws = ws;
+  return factor_sweep_multi(&item, 1, s);
+}
+
 // ----------------------------------------------------------------------------
-// Eqs. 3-5 (optionally preceded by the lower solve)
+// Lower solve alone (L z = r) on one matrix, for bta_solve(lower = 1)
 // ----------------------------------------------------------------------------
+namespace {
+__global__ void tip_fwd_kernel(int a, const double* T, double* r, const double* vT) {
+  if (threadIdx.x || blockIdx.x) return;
+  double v[kMaxTip];
+  for (int i = 0; i < a; ++i) {
+    double s = r[i] - vT[i];
+    for (int k = 0; k < i; ++k) s -= T[i + k * a] * v[k];
+    v[i] = s / T[i + i * a];
+  }
+  for (int i = 0; i < a; ++i) r[i] = v[i];
+}
+}  // namespace
+
+bta_status tip_forward(const bta_desc& q, double* rT, const double* vT, cudaStream_t s) {
+  tip_fwd_kernel<<<1, 32, 0, s>>>(q.a, q.T, rT, vT);
+  BTA_LAUNCHED();
+  return BTA_OK;
+}
+
 bta_status lower_solve(const bta_desc& q, double* z, const SweepWs& ws, cudaStream_t s) {
   const int n = q.n, ld = q.ld, a = q.a;
   const int64_t blk = (int64_t)ld * ld;
@@ -256,158 +404,203 @@ bta_status lower_solve(const bta_desc& q, double* z, const SweepWs& ws, cudaStre
       BTA_TRY(gemv_f64(h, ws.gv, s));
     }
   }
-  if (a > 0) {
-    // z_T = L_T^{-1}(r_T - v_T): reuse the tip kernel's solve on an already
-    // factored tip by running the forward substitution alone.
-    BTA_TRY(tip_forward(q, z + (int64_t)n * ld, ws.vT, s));
-  }
+  if (a > 0) BTA_TRY(tip_forward(q, z + (int64_t)n * ld, ws.vT, s));
   return BTA_OK;
 }
 
-namespace {
-__global__ void tip_fwd_kernel(int a, const double* T, double* r, const double* vT) {
-  if (threadIdx.x || blockIdx.x) return;
-  double v[kMaxTip];
-  for (int i = 0; i < a; ++i) {
-    double s = r[i] - vT[i];
-    for (int k = 0; k < i; ++k) s -= T[i + k * a] * v[k];
-    v[i] = s / T[i + i * a];
+// ----------------------------------------------------------------------------
+// Eqs. 3-5 on a set of matrices (items with a vector)
+// ----------------------------------------------------------------------------
+bta_status upper_solve_multi(const SweepItem* it, int m, cudaStream_t s) {
+  BTA_TRY(check_set(it, m));
+  const int n = it[0].q.n, ld = it[0].q.ld;
+  const int64_t blk = (int64_t)ld * ld;
+  const Groups G = make_groups(it, m);
+  if (G.vec.empty()) return BTA_OK;
+  const int c = (int)G.vec.size();
+  for (int z : G.vec) {
+    const int a = it[z].q.a;
+    if (a == 0) continue;
+    tip_kernel<<<1, 32, 0, s>>>(1, a, it[z].q.T, it[z].vec + (int64_t)n * ld, nullptr, nullptr,
+                                nullptr, 0);
+    BTA_LAUNCHED();
   }
-  for (int i = 0; i < a; ++i) r[i] = v[i];
-}
-}  // namespace
-
-bta_status tip_forward(const bta_desc& q, double* rT, const double* vT, cudaStream_t s) {
-  tip_fwd_kernel<<<1, 32, 0, s>>>(q.a, q.T, rT, vT);
-  BTA_LAUNCHED();
+  auto gv = ptrs(G.vec, [&](int z) { return it[z].ws.gv; });
+  for (int i = n - 1; i >= 0; --i) {
+    auto zi = ptrs(G.vec, [&](int z) { return it[z].vec + (int64_t)i * ld; });
+    for (int z : G.vec) {  // z_i -= L_Ci^T x_T
+      const int a = it[z].q.a;
+      if (a == 0) continue;
+      double* zz = it[z].vec + (int64_t)i * ld;
+      Gemv g; g.M = ld; g.K = a; g.A = it[z].q.C + (int64_t)i * a * ld; g.lda = a; g.transA = 1;
+      g.x = it[z].vec + (int64_t)n * ld; g.y = zz; g.yin = zz; g.alpha = -1.0; g.beta = 1.0;
+      BTA_TRY(gemv_f64(g, it[z].ws.gv, s));
+    }
+    if (i < n - 1) {  // z_i -= L_Bi^T x_{i+1}
+      auto Bi = ptrs(G.vec, [&](int z) { return it[z].q.B + i * blk; });
+      auto xn = ptrs(G.vec, [&](int z) { return it[z].vec + (int64_t)(i + 1) * ld; });
+      Gemv g; g.M = ld; g.K = ld; g.lda = ld; g.transA = 1; g.alpha = -1.0; g.beta = 1.0;
+      g.batch = c; g.Ab = cp(Bi); g.xb = cp(xn); g.yb = zi.data(); g.yinb = cp(zi);
+      g.workb = gv.data();
+      BTA_TRY(gemv_f64(g, nullptr, s));
+    }
+    {  // x_i = L_Di^{-T} z_i
+      auto Di = ptrs(G.vec, [&](int z) { return it[z].q.D + i * blk; });
+      Gemv g; g.M = ld; g.K = ld; g.lda = ld; g.transA = 1; g.triA = TRI_UPPER;
+      g.batch = c; g.Ab = cp(Di); g.xb = cp(zi); g.yb = zi.data(); g.workb = gv.data();
+      BTA_TRY(gemv_f64(g, nullptr, s));
+    }
+  }
   return BTA_OK;
 }
 
 bta_status upper_solve(const bta_desc& q, double* z, const SweepWs& ws, cudaStream_t s) {
-  const int n = q.n, ld = q.ld, a = q.a;
-  const int64_t blk = (int64_t)ld * ld;
-  double* xT = z + (int64_t)n * ld;
-  if (a > 0) {
-    tip_kernel<<<1, 32, 0, s>>>(1, a, q.T, xT, nullptr, nullptr, nullptr, 0);
-    BTA_LAUNCHED();
-  }
-  for (int i = n - 1; i >= 0; --i) {
-    double* zi = z + (int64_t)i * ld;
-    if (a > 0) {  // z_i -= L_Ci^T x_T
-      Gemv g; g.M = ld; g.K = a; g.A = q.C + (int64_t)i * a * ld; g.lda = a; g.transA = 1;
-      g.x = xT; g.y = zi; g.yin = zi; g.alpha = -1.0; g.beta = 1.0;
-      BTA_TRY(gemv_f64(g, ws.gv, s));
-    }
-    if (i < n - 1) {  // z_i -= L_Bi^T x_{i+1}
-      Gemv g; g.M = ld; g.K = ld; g.A = q.B + i * blk; g.lda = ld; g.transA = 1;
-      g.x = zi + ld; g.y = zi; g.yin = zi; g.alpha = -1.0; g.beta = 1.0;
-      BTA_TRY(gemv_f64(g, ws.gv, s));
-    }
-    // x_i = L_Di^{-T} z_i
-    Gemv g; g.M = ld; g.K = ld; g.A = q.D + i * blk; g.lda = ld; g.transA = 1;
-    g.triA = TRI_UPPER; g.x = zi; g.y = zi;
-    BTA_TRY(gemv_f64(g, ws.gv, s));
-  }
-  return BTA_OK;
+  SweepItem item;
+  item.q = q; item.vec = z; item.ws = ws;
+  return upper_solve_multi(&item, 1, s);
 }
 
 // ----------------------------------------------------------------------------
-// Selected inversion, in place, with the fused Eq. 7 reductions.
-// With F_Bi = L_Bi L_Di^{-1}, F_Ci = L_Ci L_Di^{-1}:
+// Selected inversion, in place, on a set of matrices, with the fused Eq. 7
+// reductions.  With F_Bi = L_Bi L_Di^{-1}, F_Ci = L_Ci L_Di^{-1}:
 //   Z_Ci = -Z_T F_Ci - Z_C,i+1 F_Bi
 //   Z_Bi = -Z_D,i+1 F_Bi - Z_C,i+1^T F_Ci
 //   Z_Di = L_Di^{-T} L_Di^{-1} - Z_Bi^T F_Bi - Z_Ci^T F_Ci
 // ----------------------------------------------------------------------------
-bta_status selinv_sweep(const bta_desc& q, const SweepWs& ws, const SelinvFuse* fuse,
-                        cudaStream_t s) {
-  const int n = q.n, ld = q.ld, a = q.a;
+bta_status selinv_sweep_multi(const SweepItem* it, int m, cudaStream_t s) {
+  BTA_TRY(check_set(it, m));
+  const int n = it[0].q.n, ld = it[0].q.ld;
   const int64_t blk = (int64_t)ld * ld;
-  if (a > 0) {
-    tip_kernel<<<1, 32, 0, s>>>(2, a, q.T, nullptr, nullptr, nullptr, nullptr, 0);
+  const Groups G = make_groups(it, m);
+  const int M = (int)G.all.size();
+  auto D = [&](int z, int i) { return it[z].q.D + i * blk; };
+  auto B = [&](int z, int i) { return it[z].q.B + i * blk; };
+  auto Cb = [&](int z, int i) { return it[z].q.C + (int64_t)i * it[z].q.a * ld; };
+  for (int z = 0; z < m; ++z) {
+    if (it[z].q.a == 0) continue;
+    tip_kernel<<<1, 32, 0, s>>>(2, it[z].q.a, it[z].q.T, nullptr, nullptr, nullptr, nullptr, 0);
     BTA_LAUNCHED();
   }
+  auto W1 = ptrs(G.all, [&](int z) { return it[z].ws.W1; });
+  auto W2 = ptrs(G.all, [&](int z) { return it[z].ws.W2; });
+  auto W3 = ptrs(G.all, [&](int z) { return it[z].ws.W3; });
   for (int i = n - 1; i >= 0; --i) {
-    double* Di = q.D + i * blk;
-    double* Bi = i < n - 1 ? q.B + i * blk : nullptr;
-    double* Ci = a > 0 ? q.C + (int64_t)i * a * ld : nullptr;
-    const double* Dn = i < n - 1 ? q.D + (i + 1) * blk : nullptr;      // Z_D,i+1
-    const double* Cn = (a > 0 && i < n - 1) ? q.C + (int64_t)(i + 1) * a * ld : nullptr;
-    if (Bi) {  // W1 = F_B = L_Bi L_Di^{-1}
-      Gemm g; g.M = ld; g.N = ld; g.K = ld;
-      g.A = Bi; g.lda = ld; g.B = Di; g.ldb = ld; g.triB = TRI_LOWER;
-      g.C = ws.W1; g.ldc = ld;
+    const bool hasB = i < n - 1;
+    auto Di = ptrs(G.all, [&](int z) { return D(z, i); });
+    if (hasB) {  // W1 = F_B = L_Bi L_Di^{-1}
+      auto Bi = ptrs(G.all, [&](int z) { return B(z, i); });
+      Gemm g; g.M = ld; g.N = ld; g.K = ld; g.batch = M;
+      g.Ab = cp(Bi); g.lda = ld; g.Bb = cp(Di); g.ldb = ld; g.triB = TRI_LOWER;
+      g.Cb = W1.data(); g.ldc = ld;
       BTA_TRY(gemm_f64(g, s));
     }
-    if (a > 0) {
+    for (const auto& grp : G.arrow) {
+      const int a = it[grp[0]].q.a, c = (int)grp.size();
+      auto Ci = ptrs(grp, [&](int z) { return Cb(z, i); });
+      auto Dg = ptrs(grp, [&](int z) { return D(z, i); });
+      auto Wc1 = ptrs(grp, [&](int z) { return it[z].ws.Wc1; });
+      auto Wc2 = ptrs(grp, [&](int z) { return it[z].ws.Wc2; });
+      auto T = ptrs(grp, [&](int z) { return it[z].q.T; });
       {  // Wc1 = F_C = L_Ci L_Di^{-1}
-        Gemm g; g.M = a; g.N = ld; g.K = ld;
-        g.A = Ci; g.lda = a; g.B = Di; g.ldb = ld; g.triB = TRI_LOWER;
-        g.C = ws.Wc1; g.ldc = a;
+        Gemm g; g.M = a; g.N = ld; g.K = ld; g.batch = c;
+        g.Ab = cp(Ci); g.lda = a; g.Bb = cp(Dg); g.ldb = ld; g.triB = TRI_LOWER;
+        g.Cb = Wc1.data(); g.ldc = a;
         BTA_TRY(gemm_f64(g, s));
       }
       {  // Wc2 = -Z_T F_C
-        Gemm g; g.M = a; g.N = ld; g.K = a;
-        g.A = q.T; g.lda = a; g.B = ws.Wc1; g.ldb = a;
-        g.C = ws.Wc2; g.ldc = a; g.alpha = -1.0;
+        Gemm g; g.M = a; g.N = ld; g.K = a; g.batch = c;
+        g.Ab = cp(T); g.lda = a; g.Bb = cp(Wc1); g.ldb = a;
+        g.Cb = Wc2.data(); g.ldc = a; g.alpha = -1.0;
         BTA_TRY(gemm_f64(g, s));
       }
-      if (Bi) {  // Wc2 -= Z_C,i+1 F_B
-        Gemm g; g.M = a; g.N = ld; g.K = ld;
-        g.A = Cn; g.lda = a; g.B = ws.W1; g.ldb = ld;
-        g.C = ws.Wc2; g.ldc = a; g.Cin = ws.Wc2; g.ldcin = a; g.alpha = -1.0; g.beta = 1.0;
+      if (hasB) {  // Wc2 -= Z_C,i+1 F_B
+        auto Cn = ptrs(grp, [&](int z) { return Cb(z, i + 1); });
+        auto W1g = ptrs(grp, [&](int z) { return it[z].ws.W1; });
+        Gemm g; g.M = a; g.N = ld; g.K = ld; g.batch = c;
+        g.Ab = cp(Cn); g.lda = a; g.Bb = cp(W1g); g.ldb = ld;
+        g.Cb = Wc2.data(); g.ldc = a; g.Cinb = cp(Wc2); g.ldcin = a; g.alpha = -1.0;
+        g.beta = 1.0;
         BTA_TRY(gemm_f64(g, s));
       }
     }
-    if (Bi) {
+    if (hasB) {
       {  // W2 = Z_B = -Z_D,i+1 F_B
-        Gemm g; g.M = ld; g.N = ld; g.K = ld;
-        g.A = Dn; g.lda = ld; g.B = ws.W1; g.ldb = ld;
-        g.C = ws.W2; g.ldc = ld; g.alpha = -1.0;
+        auto Dn = ptrs(G.all, [&](int z) { return D(z, i + 1); });
+        Gemm g; g.M = ld; g.N = ld; g.K = ld; g.batch = M;
+        g.Ab = cp(Dn); g.lda = ld; g.Bb = cp(W1); g.ldb = ld;
+        g.Cb = W2.data(); g.ldc = ld; g.alpha = -1.0;
         BTA_TRY(gemm_f64(g, s));
       }
-      if (a > 0) {  // W2 -= Z_C,i+1^T F_C
-        Gemm g; g.M = ld; g.N = ld; g.K = a;
-        g.A = Cn; g.lda = a; g.transA = 1; g.B = ws.Wc1; g.ldb = a;
-        g.C = ws.W2; g.ldc = ld; g.Cin = ws.W2; g.ldcin = ld; g.alpha = -1.0; g.beta = 1.0;
+      for (const auto& grp : G.arrow) {  // W2 -= Z_C,i+1^T F_C
+        const int a = it[grp[0]].q.a, c = (int)grp.size();
+        auto Cn = ptrs(grp, [&](int z) { return Cb(z, i + 1); });
+        auto Wc1 = ptrs(grp, [&](int z) { return it[z].ws.Wc1; });
+        auto W2g = ptrs(grp, [&](int z) { return it[z].ws.W2; });
+        Gemm g; g.M = ld; g.N = ld; g.K = a; g.batch = c;
+        g.Ab = cp(Cn); g.lda = a; g.transA = 1; g.Bb = cp(Wc1); g.ldb = a;
+        g.Cb = W2g.data(); g.ldc = ld; g.Cinb = cp(W2g); g.ldcin = ld; g.alpha = -1.0;
+        g.beta = 1.0;
         BTA_TRY(gemm_f64(g, s));
       }
     }
     {  // W3 = L_Di^{-T} L_Di^{-1} (lower part)
-      Gemm g; g.M = ld; g.N = ld; g.K = ld;
-      g.A = Di; g.lda = ld; g.transA = 1; g.triA = TRI_UPPER;
-      g.B = Di; g.ldb = ld; g.triB = TRI_LOWER;
-      g.C = ws.W3; g.ldc = ld; g.out_lower = 1;
+      Gemm g; g.M = ld; g.N = ld; g.K = ld; g.batch = M;
+      g.Ab = cp(Di); g.lda = ld; g.transA = 1; g.triA = TRI_UPPER;
+      g.Bb = cp(Di); g.ldb = ld; g.triB = TRI_LOWER;
+      g.Cb = W3.data(); g.ldc = ld; g.out_lower = 1;
       BTA_TRY(gemm_f64(g, s));
     }
-    if (Bi) {  // W3 -= Z_B^T F_B
-      Gemm g; g.M = ld; g.N = ld; g.K = ld;
-      g.A = ws.W2; g.lda = ld; g.transA = 1; g.B = ws.W1; g.ldb = ld;
-      g.C = ws.W3; g.ldc = ld; g.Cin = ws.W3; g.ldcin = ld; g.alpha = -1.0; g.beta = 1.0;
+    if (hasB) {  // W3 -= Z_B^T F_B
+      Gemm g; g.M = ld; g.N = ld; g.K = ld; g.batch = M;
+      g.Ab = cp(W2); g.lda = ld; g.transA = 1; g.Bb = cp(W1); g.ldb = ld;
+      g.Cb = W3.data(); g.ldc = ld; g.Cinb = cp(W3); g.ldcin = ld; g.alpha = -1.0; g.beta = 1.0;
       g.out_lower = 1;
       BTA_TRY(gemm_f64(g, s));
     }
-    if (a > 0) {  // W3 -= Z_C^T F_C
-      Gemm g; g.M = ld; g.N = ld; g.K = a;
-      g.A = ws.Wc2; g.lda = a; g.transA = 1; g.B = ws.Wc1; g.ldb = a;
-      g.C = ws.W3; g.ldc = ld; g.Cin = ws.W3; g.ldcin = ld; g.alpha = -1.0; g.beta = 1.0;
+    for (const auto& grp : G.arrow) {  // W3 -= Z_C^T F_C
+      const int a = it[grp[0]].q.a, c = (int)grp.size();
+      auto Wc1 = ptrs(grp, [&](int z) { return it[z].ws.Wc1; });
+      auto Wc2 = ptrs(grp, [&](int z) { return it[z].ws.Wc2; });
+      auto W3g = ptrs(grp, [&](int z) { return it[z].ws.W3; });
+      Gemm g; g.M = ld; g.N = ld; g.K = a; g.batch = c;
+      g.Ab = cp(Wc2); g.lda = a; g.transA = 1; g.Bb = cp(Wc1); g.ldb = a;
+      g.Cb = W3g.data(); g.ldc = ld; g.Cinb = cp(W3g); g.ldcin = ld; g.alpha = -1.0; g.beta = 1.0;
       g.out_lower = 1;
       BTA_TRY(gemm_f64(g, s));
     }
-    BTA_TRY(copy_block(ws.W3, ld, Di, ld, ld, ld, 1.0, 1, s));       // Z_D (full)
-    if (Bi) BTA_TRY(copy_block(ws.W2, ld, Bi, ld, ld, ld, 1.0, 0, s));
-    if (a > 0) BTA_TRY(copy_block(ws.Wc2, a, Ci, a, a, ld, 1.0, 0, s));
-    if (fuse) {
-      const ModelDev& md = *fuse->md;
+    BTA_TRY(copy_block_batch(M, cp(W3), ld, Di.data(), ld, ld, ld, 1.0, 1, s));   // Z_D (full)
+    if (hasB) {
+      auto Bi = ptrs(G.all, [&](int z) { return B(z, i); });
+      BTA_TRY(copy_block_batch(M, cp(W2), ld, Bi.data(), ld, ld, ld, 1.0, 0, s));
+    }
+    for (const auto& grp : G.arrow) {
+      const int a = it[grp[0]].q.a, c = (int)grp.size();
+      auto Wc2 = ptrs(grp, [&](int z) { return it[z].ws.Wc2; });
+      auto Ci = ptrs(grp, [&](int z) { return Cb(z, i); });
+      BTA_TRY(copy_block_batch(c, cp(Wc2), a, Ci.data(), a, a, ld, 1.0, 0, s));
+    }
+    for (int z = 0; z < m; ++z) {
+      const SelinvFuse* fz = it[z].fuse;
+      if (!fz) continue;
+      const ModelDev& md = *fz->md;
       const int kk = md.k * md.k, pch = pattern_chunks(md);
-      BTA_TRY(launch_pattern_dot(md, Di, fuse->counts, i, fuse->PD + (int64_t)i * kk * pch * kNP,
+      BTA_TRY(launch_pattern_dot(md, D(z, i), fz->counts, i,
+                                 fz->PD + (int64_t)i * kk * pch * kNP, s));
+      if (hasB)
+        BTA_TRY(launch_pattern_dot(md, B(z, i), 0, i, fz->PB + (int64_t)i * kk * pch * kNP, s));
+      if (it[z].q.a > 0 && fz->PC)
+        BTA_TRY(launch_arrow_dot(md, Cb(z, i), i, fz->PC + (int64_t)i * md.k * arrow_chunks(md),
                                  s));
-      if (Bi)
-        BTA_TRY(launch_pattern_dot(md, Bi, 0, i, fuse->PB + (int64_t)i * kk * pch * kNP, s));
-      if (a > 0 && fuse->PC)
-        BTA_TRY(launch_arrow_dot(md, Ci, i, fuse->PC + (int64_t)i * md.k * arrow_chunks(md), s));
     }
   }
   return BTA_OK;
+}
+
+bta_status selinv_sweep(const bta_desc& q, const SweepWs& ws, const SelinvFuse* fuse,
+                        cudaStream_t s) {
+  SweepItem item;
+  item.q = q; item.ws = ws; item.fuse = fuse;
+  return selinv_sweep_multi(&item, 1, s);
 }
 
 }  // namespace bta

@@ -25,6 +25,24 @@ struct SelinvFuse {
 
 int logdet_slots(int n, int ld);   // n * (ld / 32) + 1 (tip)
 
+// One matrix of a set swept together.  All matrices of a set share n and ld;
+// the arrow width may differ (Q_c with a > 0 next to the block-tridiagonal
+// Q_p).  Every block step of the sweep is then one launch over the set.
+struct SweepItem {
+  bta_desc q{};
+  double* vec = nullptr;           // factor: rhs -> z (or null); solves: z -> x
+  double* slots = nullptr;         // factor: log-det slots
+  int32_t* fail = nullptr;         // factor: failure flag (first failing block)
+  SweepWs ws;
+  const SelinvFuse* fuse = nullptr;   // selected inversion: fused Eq. 7 sums (or null)
+};
+// mark (optional): recorded on s right after block 0's diagonal factor, so a
+// concurrent sweep can start one diagonal step behind this one.
+bta_status factor_sweep_multi(const SweepItem* items, int m, cudaStream_t s,
+                              cudaEvent_t mark = nullptr);
+bta_status upper_solve_multi(const SweepItem* items, int m, cudaStream_t s);
+bta_status selinv_sweep_multi(const SweepItem* items, int m, cudaStream_t s);
+
 bta_status factor_sweep(const bta_desc& q, double* rhs, double* slots, int32_t* fail,
                         const SweepWs& ws, cudaStream_t s);
 bta_status lower_solve(const bta_desc& q, double* z, const SweepWs& ws, cudaStream_t s);

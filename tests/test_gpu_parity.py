@@ -103,6 +103,23 @@ def test_batch_of_thetas_equals_single_calls(P):
         np.testing.assert_array_equal(g, gb[i])
 
 
+@pytest.mark.parametrize("name", ["st_tiny", "coreg_tiny"])
+def test_concurrent_batch_equals_single_calls(P, name):
+    # A batch evaluated together (all matrices in the same launches) gives the
+    # same bits as one theta at a time: each product accumulates over k in
+    # the same order whatever the tile shape the batch size selects.
+    prob = workloads.make_problem(name)
+    m = P.InlaModel(prob)
+    pts = workloads.fd_stencil(prob.theta, 1e-3)
+    for grad in (True, False):
+        fb, gb = m.value_and_grad(pts, grad=grad, concurrent=5)
+        for i in range(pts.shape[0]):
+            f, g = m.value_and_grad(pts[i], grad=grad)
+            assert f == fb[i]
+            if grad:
+                np.testing.assert_array_equal(g, gb[i])
+
+
 def test_gradient_matches_gpu_central_fd(P):
     prob = workloads.make_problem("coreg_k2_small")
     m = P.InlaModel(prob)
