@@ -227,6 +227,22 @@ bta_status bta_gemm(int32_t M, int32_t N, int32_t K, double alpha, const double*
                     double* C, int32_t ldc, cudaStream_t stream);
 
 /*
+ * bta_gemm_mixed -- the same product as bta_gemm, computed in split
+ * precision on the tensor cores (the off-diagonal Schur-complement products
+ * of the mixed-precision mode): each FP64 operand is carried as a pair of
+ * TF32 values hi + lo, three TF32 products (hi*hi, hi*lo, lo*hi) accumulate
+ * in FP32, the result is combined with alpha and beta in FP64.  Relative
+ * error per entry ~1e-6 of sum |A||B|.  status (device int32, may be NULL)
+ * receives BTA_ERR_TIMEOUT if a bounded wait in the kernel expired (0 is
+ * never written: initialise it).  Allocates its operand copies with
+ * cudaMallocAsync on the stream.
+ */
+bta_status bta_gemm_mixed(int32_t M, int32_t N, int32_t K, double alpha, const double* A,
+                          int32_t lda, int32_t transA, const double* B, int32_t ldb,
+                          int32_t transB, double beta, double* C, int32_t ldc, int32_t* status,
+                          cudaStream_t stream);
+
+/*
  * inla_grid_stencil -- spatial base matrices of an nx x ny grid model
  * (Section II-A): Cm = I, G = 5-point graph Laplacian with natural boundary,
  * GG = G G, all on GG's 13-point pattern, CSR with sorted columns (host

@@ -73,6 +73,9 @@ SIGNATURES = {
     "bta_gemm": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_void_p, C.c_int32,
                            C.c_int32, C.c_void_p, C.c_int32, C.c_int32, C.c_double, C.c_void_p,
                            C.c_int32, C.c_void_p]),
+    "bta_gemm_mixed": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_void_p,
+                                 C.c_int32, C.c_int32, C.c_void_p, C.c_int32, C.c_int32,
+                                 C.c_double, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "inla_grid_stencil": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(C.c_int32), C.c_void_p,
                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
 }

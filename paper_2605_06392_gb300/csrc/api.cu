@@ -604,6 +604,23 @@ bta_status bta_gemm(int32_t M, int32_t N, int32_t K, double alpha, const double*
   return gemm_f64(g, stream);
 }
 
+bta_status bta_gemm_mixed(int32_t M, int32_t N, int32_t K, double alpha, const double* A,
+                          int32_t lda, int32_t transA, const double* B, int32_t ldb,
+                          int32_t transB, double beta, double* Cm, int32_t ldc, int32_t* status,
+                          cudaStream_t stream) {
+  if (M < 0 || N < 0 || K < 1 || !A || !B || !Cm) return BTA_ERR_ARG;
+  Gemm g;
+  g.M = M; g.N = N; g.K = K; g.alpha = alpha; g.beta = beta;
+  g.A = A; g.lda = lda; g.transA = transA ? 1 : 0;
+  g.B = B; g.ldb = ldb; g.transB = transB ? 1 : 0;
+  g.C = Cm; g.ldc = ldc; g.Cin = Cm; g.ldcin = ldc;
+  void* ws = nullptr;
+  BTA_CUDA_TRY(cudaMallocAsync(&ws, tc_gemm_ws_bytes(M, N, K), stream));
+  bta_status st = tc_gemm_mixed(g, ws, status, stream);
+  cudaFreeAsync(ws, stream);
+  return st;
+}
+
 bta_status inla_last_parts(const inla_model* m, double* parts, double* phases) {
   if (!m || m->last.empty()) return BTA_ERR_STATE;
   const double* p = m->last.data() + 1 + m->d;

@@ -126,6 +126,13 @@ struct Gemv {
 bta_status gemv_f64(const Gemv& g, double* work, cudaStream_t s);
 constexpr int kGemvSplit = 16;      // K splits; work needs kGemvSplit * M doubles
 
+// Split-precision (3xTF32) tensor-core GEMM (tc_gemm.cu): same contract as
+// gemm_f64 for a single problem; ws holds tc_gemm_ws_bytes(M, N, K) bytes;
+// *status (device, may be null) receives BTA_ERR_TIMEOUT if a bounded wait
+// inside the kernel expired.
+bta_status tc_gemm_mixed(const Gemm& g, void* ws, int32_t* status, cudaStream_t s);
+size_t tc_gemm_ws_bytes(int M, int N, int K);
+
 // ----------------------------------------------------------------------------
 // Diagonal-block Cholesky + inverse (potrf.cu)
 // On return the lower triangle of A (n x n, ld) holds L^{-1} where A = L L^T;

@@ -1,0 +1,371 @@
+// Split-precision tensor-core GEMM for the mixed-precision sweeps (sm_103a):
+//   C = alpha op(A) op(B) + beta C,  FP64 in and out,
+// computed on tcgen05 tensor cores with TF32 operands and FP32 accumulation
+// in tensor memory, each FP64 operand carried as a pair hi + lo of TF32
+// values ("3xTF32": hi*hi + hi*lo + lo*hi, about 22 significant bits per
+// product, against 11 for one TF32 product).
+//
+// Pipeline per 128 x 128 output tile (one CTA, 128 threads):
+//   * a split kernel writes op(A) and op(B)^T as K-major FP32 hi/lo arrays;
+//   * warp 0 lane 0 streams 32-wide K slabs of the four operand tiles into a
+//     3-stage shared-memory ring with TMA (128-byte swizzle), signalling a
+//     "full" mbarrier with the transaction byte count;
+//   * warp 1 lane 0 issues 12 tcgen05.mma (kind::tf32, M=128, N=128, K=8) per
+//     slab into one TMEM accumulator and releases the slab with
+//     tcgen05.commit on its "empty" mbarrier;
+//   * all four warps read the accumulator back with tcgen05.ld (one warp per
+//     32 TMEM lanes) and apply alpha / beta in FP64.
+// Every mbarrier wait is bounded: on expiry the kernel records
+// BTA_ERR_TIMEOUT in a status word, stops issuing work, still waits (bounded)
+// for the MMAs it issued and frees its tensor memory.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "common.cuh"
+
+namespace bta {
+namespace {
+
+constexpr int TM = 128, TN = 128, TK = 32;          // tile rows, cols, fp32 per K slab
+constexpr int kStages = 3;
+constexpr int kTileBytes = TM * TK * 4;             // 16 KB: one operand tile of one slab
+constexpr int kStageBytes = 4 * kTileBytes;         // Ahi, Alo, Bhi, Blo
+constexpr int kTcThreads = 128;
+constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 128;
+constexpr uint32_t kTmemCols = 128;                 // 128 lanes x 128 fp32 columns
+constexpr long long kWaitLimit = 1ll << 21;          // bounded mbarrier polls (~1 s)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t addr, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t addr, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(addr), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(addr), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait; false when the limit expired.
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
+  for (long long it = 0; it < kWaitLimit; ++it)
+    if (mbar_try_wait(addr, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t mbar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(mbar), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle,
+// 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);     // start address
+  d |= (uint64_t)1 << 16;                       // leading-dimension offset (unused here)
+  d |= (uint64_t)(1024 >> 4) << 32;             // stride between 8-row groups
+  d |= (uint64_t)1 << 46;                       // descriptor version
+  d |= (uint64_t)2 << 61;                       // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: kind::tf32, FP32 accumulator, both operands
+// K-major, M = 128, N = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(TN >> 3) << 17) |
+                            ((uint32_t)(TM >> 4) << 24);
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+struct TcArgs {
+  int M, N, K;
+  double alpha, beta;
+  double* C;
+  int ldc;
+  const double* Cin;
+  int ldcin;
+  int out_lower;
+  int32_t* status;
+};
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+    tc_gemm_tf32x3_kernel(const __grid_constant__ CUtensorMap mAhi,
+                          const __grid_constant__ CUtensorMap mAlo,
+                          const __grid_constant__ CUtensorMap mBhi,
+                          const __grid_constant__ CUtensorMap mBlo, TcArgs g) {
+  const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
+  if (g.out_lower && n0 > m0 + TM - 1) return;   // whole CTA exits before any set-up
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
+  // bars[0..S): full, bars[S..2S): empty, bars[2S]: done
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 1);
+  __shared__ int s_abort;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nk = (g.K + TK - 1) / TK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(smem_u32(&bars[s]), 1);
+      mbar_init(smem_u32(&bars[kStages + s]), 1);
+    }
+    mbar_init(smem_u32(&bars[2 * kStages]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_abort = 0;
+  }
+  __syncwarp();
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer
+    for (int kt = 0; kt < nk; ++kt) {
+      const int s = kt % kStages;
+      if (kt >= kStages &&
+          !mbar_wait(smem_u32(&bars[kStages + s]), (uint32_t)((kt / kStages - 1) & 1))) {
+        s_abort = 1;
+        break;
+      }
+      if (*(volatile int*)&s_abort) break;
+      const uint32_t full = smem_u32(&bars[s]);
+      mbar_expect_tx(full, kStageBytes);
+      uint8_t* st = smem + s * kStageBytes;
+      const int k0 = kt * TK;
+      tma_load_2d(smem_u32(st), &mAhi, full, k0, m0);
+      tma_load_2d(smem_u32(st + kTileBytes), &mAlo, full, k0, m0);
+      tma_load_2d(smem_u32(st + 2 * kTileBytes), &mBhi, full, k0, n0);
+      tma_load_2d(smem_u32(st + 3 * kTileBytes), &mBlo, full, k0, n0);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer
+    int issued = 0;
+    for (int kt = 0; kt < nk; ++kt) {
+      const int s = kt % kStages;
+      if (!mbar_wait(smem_u32(&bars[s]), (uint32_t)((kt / kStages) & 1))) {
+        s_abort = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t base = smem_u32(smem + s * kStageBytes);
+#pragma unroll
+      for (int kk = 0; kk < TK / 8; ++kk) {
+        const uint32_t off = kk * 32;   // 8 fp32 = 32 bytes along K inside the swizzle atom
+        const uint64_t ahi = sdesc(base + off), alo = sdesc(base + kTileBytes + off);
+        const uint64_t bhi = sdesc(base + 2 * kTileBytes + off);
+        const uint64_t blo = sdesc(base + 3 * kTileBytes + off);
+        mma_tf32(tmem, ahi, bhi, issued++ > 0);
+        mma_tf32(tmem, ahi, blo, 1);
+        mma_tf32(tmem, alo, bhi, 1);
+      }
+      mma_commit(smem_u32(&bars[kStages + s]));   // slab s free once these MMAs finish
+    }
+    mma_commit(smem_u32(&bars[2 * kStages]));     // accumulator complete
+  }
+  __syncwarp();
+  // ---- epilogue: all four warps (the decision below is uniform per CTA)
+  const bool done = mbar_wait(smem_u32(&bars[2 * kStages]), 0);
+  const int failed = __syncthreads_or(!done || s_abort);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (failed) {
+    if (threadIdx.x == 0 && g.status) atomicExch(g.status, (int)BTA_ERR_TIMEOUT);
+  } else {
+    const int m = m0 + warp * 32 + lane;
+    for (int c = 0; c < TN; c += 32) {
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, v);
+      if (m < g.M) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int n = n0 + c + j;
+          if (n >= g.N || (g.out_lower && m < n)) continue;
+          double out = g.alpha * (double)v[j];
+          if (g.beta != 0.0) out = fma(g.beta, g.Cin[m + (int64_t)n * g.ldcin], out);
+          g.C[m + (int64_t)n * g.ldc] = out;
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kTmemCols)
+                 : "memory");
+  }
+}
+
+// Y (rows x Kp, row-major fp32 hi/lo) = split(op(X)) with
+// op(X)[r][k] = trans ? X[k + r*ldx] : X[r + k*ldx], masked to its triangle.
+__global__ void split_tf32_kernel(int rows, int K, int Kp, const double* __restrict__ X, int ldx,
+                                  int trans, int tri, float* __restrict__ hi,
+                                  float* __restrict__ lo) {
+  __shared__ double t[32][33];
+  const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+  for (int yy = ty; yy < 32; yy += 8) {
+    // coalesced read: consecutive tx walk the contiguous index of X
+    int r, k;
+    if (!trans) { r = r0 + tx; k = k0 + yy; } else { k = k0 + tx; r = r0 + yy; }
+    double v = 0.0;
+    if (r < rows && k < K) {
+      const bool zero = (tri == TRI_LOWER && k > r) || (tri == TRI_UPPER && k < r);
+      if (!zero) v = trans ? X[k + (int64_t)r * ldx] : X[r + (int64_t)k * ldx];
+    }
+    if (!trans) t[tx][yy] = v; else t[yy][tx] = v;   // t[r - r0][k - k0]
+  }
+  __syncthreads();
+  for (int yy = ty; yy < 32; yy += 8) {
+    const int r = r0 + yy, k = k0 + tx;
+    if (r >= rows || k >= Kp) continue;
+    const double v = t[yy][tx];
+    uint32_t hb, lb;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"((float)v));
+    const float h = __uint_as_float(hb);
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lb) : "f"((float)(v - (double)h)));
+    const float l = __uint_as_float(lb);
+    hi[(int64_t)r * Kp + k] = h;
+    lo[(int64_t)r * Kp + k] = l;
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::mutex g_encode_mu;
+
+bta_status get_encode() {
+  std::lock_guard<std::mutex> lock(g_encode_mu);
+  if (g_encode) return BTA_OK;
+  cudaDriverEntryPointQueryResult q;
+  void* fn = nullptr;
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                   cudaEnableDefault, &q);
+  if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return BTA_ERR_CUDA;
+  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  return BTA_OK;
+}
+
+// 2D map over a row-major fp32 array rows x Kp, box 32 (K) x 128 (rows).
+bta_status make_map(CUtensorMap* map, const float* base, int rows, int Kp) {
+  cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)Kp * sizeof(float)};
+  cuuint32_t box[2] = {TK, TM};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims,
+                        strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? BTA_OK : BTA_ERR_ARG;
+}
+
+}  // namespace
+
+size_t tc_gemm_ws_bytes(int M, int N, int K) {
+  const size_t Kp = (size_t)(K + 3) / 4 * 4;
+  return 2 * ((size_t)M + N) * Kp * sizeof(float) + 256;
+}
+
+bta_status tc_gemm_mixed(const Gemm& g, void* ws, int32_t* status, cudaStream_t s) {
+  if (g.M <= 0 || g.N <= 0) return BTA_OK;
+  if (g.batch != 1 || g.Ab || !g.A || !g.B || !g.C || g.K < 1 || !ws) return BTA_ERR_ARG;
+  BTA_TRY(get_encode());
+  const int M = g.M, N = g.N, K = g.K;
+  const int Kp = (K + 3) / 4 * 4;
+  float* Ahi = reinterpret_cast<float*>(
+      (reinterpret_cast<uintptr_t>(ws) + 255) & ~(uintptr_t)255);
+  float* Alo = Ahi + (size_t)M * Kp;
+  float* Bhi = Alo + (size_t)M * Kp;
+  float* Blo = Bhi + (size_t)N * Kp;
+  {
+    dim3 grid(cdiv(Kp, 32), cdiv(M, 32));
+    split_tf32_kernel<<<grid, dim3(32, 8), 0, s>>>(M, K, Kp, g.A, g.lda, g.transA, g.triA, Ahi,
+                                                   Alo);
+    BTA_LAUNCHED();
+  }
+  {
+    // rows of op(B)^T: Y[n][k] = op(B)[k][n]; the mask flips with the transpose
+    const int trib = g.triB == TRI_LOWER ? TRI_UPPER : g.triB == TRI_UPPER ? TRI_LOWER : TRI_NONE;
+    dim3 grid(cdiv(Kp, 32), cdiv(N, 32));
+    split_tf32_kernel<<<grid, dim3(32, 8), 0, s>>>(N, K, Kp, g.B, g.ldb, !g.transB, trib, Bhi,
+                                                   Blo);
+    BTA_LAUNCHED();
+  }
+  CUtensorMap mAhi, mAlo, mBhi, mBlo;
+  BTA_TRY(make_map(&mAhi, Ahi, M, Kp));
+  BTA_TRY(make_map(&mAlo, Alo, M, Kp));
+  BTA_TRY(make_map(&mBhi, Bhi, N, Kp));
+  BTA_TRY(make_map(&mBlo, Blo, N, Kp));
+  static bool attr_set = false;
+  if (!attr_set) {
+    BTA_CUDA_TRY(cudaFuncSetAttribute(tc_gemm_tf32x3_kernel,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+    attr_set = true;
+  }
+  TcArgs a;
+  a.M = M; a.N = N; a.K = K; a.alpha = g.alpha; a.beta = g.beta; a.C = g.C; a.ldc = g.ldc;
+  a.Cin = g.Cin ? g.Cin : g.C; a.ldcin = g.Cin ? g.ldcin : g.ldc; a.out_lower = g.out_lower;
+  a.status = status;
+  dim3 grid(cdiv(M, TM), cdiv(N, TN));
+  tc_gemm_tf32x3_kernel<<<grid, kTcThreads, kSmemBytes, s>>>(mAhi, mAlo, mBhi, mBlo, a);
+  BTA_LAUNCHED();
+  return BTA_OK;
+}
+
+}  // namespace bta
