@@ -268,6 +268,31 @@ def main():
             fvb, _ = model.value_and_grad(pts, grad=False, concurrent=pts.shape[0])
         t_fdb = (time.perf_counter() - t0) / args.fd_steps
 
+    # --- mixed precision (tensor-core split-TF32 Schur products, FP64 diagonal
+    # factors / log-dets / refinement): time and error against the FP64 path
+    x64 = model.mode().cpu().numpy()
+    parts64 = model.last_parts()
+    for _ in range(2):
+        fm, gm = model.value_and_grad(theta, precision=1)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        fm, gm = model.value_and_grad(theta, precision=1)
+    e1.record(stream)
+    e1.synchronize()
+    t_mixed = e0.elapsed_time(e1) / args.steps * 1e-3
+    xm = model.mode().cpu().numpy()
+    pm = model.last_parts()
+    gscale = np.maximum(np.abs(g), np.abs(parts64["phase_a"]) + np.abs(parts64["phase_b"]) +
+                        np.abs(parts64["phase_c"]))
+    mixed = {"ms_per_step": 1e3 * t_mixed, "gradients_per_s": 1.0 / t_mixed,
+             "speedup_vs_fp64": t_step / t_mixed,
+             "rel_err_f": abs(fm - f) / abs(f),
+             "rel_err_x": float(np.max(np.abs(xm - x64)) / np.max(np.abs(x64))),
+             "rel_err_grad": [float(v) for v in np.abs(gm - g) / gscale],
+             "reference": "FP64 GPU path of this run (itself within 1e-10 of the FP64 oracle)"}
+    del pm
+
     # --- dominant kernel roofline
     gemm_ms, gemm_tf = gemm_roofline(P, torch, prob.b)
 
@@ -299,6 +324,7 @@ def main():
                             "speedup_ad_vs_batched_fd": t_fdb / t_step,
                             "max_rel_diff_fd_vs_ad": float(np.max(np.abs(g_fd - g) /
                                                                   np.maximum(np.abs(g), 1.0)))},
+            "mixed_precision": mixed,
             "fp64_step": {"algorithmic_tflop_per_step": flops_grad / 1e12,
                           "achieved_tflops": step_tf, "frac_of_peak": step_tf / FP64_PEAK_TFLOPS},
             "roofline": {"bound": "alu", "kernel": "gemm_f64_kernel<32,32> at b x b x b",

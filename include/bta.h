@@ -102,7 +102,12 @@ typedef struct inla_model inla_model;
 
 /* Options for inla_value_and_grad. */
 typedef struct {
-  int32_t precision;   /* 0: FP64 everywhere (the only mode in this build)  */
+  int32_t precision;   /* 0: FP64 everywhere.  1: mixed -- the b x b
+                          off-diagonal Schur products of both factorisations
+                          and the selected-inversion products in split TF32
+                          on the tensor cores (FP32 accumulation); diagonal
+                          block factorisation, log-determinants, arrow and tip
+                          in FP64; one FP64 refinement step on x*            */
   int32_t use_graph;   /* 1: capture the evaluation in a CUDA graph, replay */
   int32_t streams;     /* thetas evaluated together for batch > 1 (1..16): their
                           matrices are swept in the same batched launches;

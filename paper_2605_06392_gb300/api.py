@@ -98,9 +98,9 @@ class InlaModel:
 
     # -- evaluation ----------------------------------------------------------
     def value_and_grad(self, theta, grad: bool = True, use_graph: bool = True, stream=None,
-                       concurrent: int = 1):
+                       concurrent: int = 1, precision: int = 0):
         return inla_value_and_grad(self, theta, grad=grad, use_graph=use_graph, stream=stream,
-                                   concurrent=concurrent)
+                                   concurrent=concurrent, precision=precision)
 
     def value(self, theta, use_graph: bool = True, stream=None):
         return inla_value_and_grad(self, theta, grad=False, use_graph=use_graph,
@@ -202,18 +202,21 @@ def bta_selinv(L: BtaMatrix, model: InlaModel | None = None, theta=None, which: 
 
 
 def inla_value_and_grad(model: InlaModel, theta, grad: bool = True, use_graph: bool = True,
-                        stream=None, concurrent: int = 1):
+                        stream=None, concurrent: int = 1, precision: int = 0):
     """f(theta) (Eq. 1) and its gradient (Eq. 6) for one theta (d,) or a
     batch (B, d).  With concurrent > 1, up to that many thetas are evaluated
     together (their matrices swept in the same launches; each needs its own
-    device buffers).  Returns numpy arrays (f, grad or None)."""
+    device buffers).  precision 1 selects the mixed-precision mode (tensor-core
+    split-TF32 Schur products, FP64 diagonal factors and log-dets, one FP64
+    refinement of x*).  Returns numpy arrays (f, grad or None)."""
     th = np.ascontiguousarray(np.atleast_2d(np.asarray(theta, dtype=np.float64)))
     batch = th.shape[0]
     if th.shape[1] != model.d:
         raise ValueError(f"theta must have {model.d} columns")
     f = np.zeros(batch)
     g = np.zeros((batch, model.d)) if grad else None
-    opts = inla_opts(precision=0, use_graph=int(use_graph), streams=int(concurrent), reserved=0)
+    opts = inla_opts(precision=int(precision), use_graph=int(use_graph), streams=int(concurrent),
+                     reserved=0)
     dp = C.POINTER(C.c_double)
     check(lib().inla_value_and_grad(model.handle, th.ctypes.data_as(dp), batch,
                                     f.ctypes.data_as(dp),

@@ -36,11 +36,12 @@ struct EvalCtx {
   double* out = nullptr;
   SweepWs wsc, wsp;
   SelinvFuse fc, fp;
+  double* dr = nullptr;         // mixed mode: refinement residual / correction
   int have_factors = 0;         // last evaluation was value-only: factors still held
 };
 
 struct GraphKey {
-  int mode, count;
+  int mode, count, precision;
   cudaGraphExec_t exec;
   int64_t kernels;
 };
@@ -110,7 +111,7 @@ bta_status ctx_alloc(inla_model* m, EvalCtx& c) {
   BTA_TRY(dmalloc(m, &c.x, (size_t)nt * ld + a));
   BTA_TRY(dmalloc(m, &c.slots_c, m->nslots));
   BTA_TRY(dmalloc(m, &c.slots_p, m->nslots));
-  BTA_TRY(dmalloc(m, &c.fail, 2));
+  BTA_TRY(dmalloc(m, &c.fail, 4));   // [0] Q_c pivot, [1] Q_p pivot, [2] tensor-core status
   const size_t pblk = (size_t)k * k * pattern_chunks(md) * kNP;
   BTA_TRY(dmalloc(m, &c.PDc, nt * pblk));
   BTA_TRY(dmalloc(m, &c.PBc, std::max(nt - 1, 1) * pblk));
@@ -127,6 +128,15 @@ bta_status ctx_alloc(inla_model* m, EvalCtx& c) {
   BTA_TRY(dmalloc(m, &wsbuf, 2 * wsb));
   c.wsc.carve(wsbuf, ld, a);
   c.wsp.carve(wsbuf + wsb, ld, a);
+  // mixed precision: operand copies of the tensor-core products, one per sweep
+  const size_t tcb = tc_gemm_ws_bytes(ld, ld, ld);
+  uint8_t* tcbuf = nullptr;
+  BTA_TRY(dmalloc(m, &tcbuf, 2 * tcb));
+  c.wsc.tc = tcbuf;
+  c.wsp.tc = tcbuf + tcb;
+  c.wsc.tcstat = c.fail + 2;
+  c.wsp.tcstat = c.fail + 2;
+  BTA_TRY(dmalloc(m, &c.dr, (size_t)nt * ld + a));
   c.fc.md = &m->md; c.fc.counts = 1; c.fc.PD = c.PDc; c.fc.PB = c.PBc; c.fc.PC = c.PCc;
   c.fp.md = &m->md; c.fp.counts = 0; c.fp.PD = c.PDp; c.fp.PB = c.PBp; c.fp.PC = nullptr;
   return BTA_OK;
@@ -156,7 +166,7 @@ bta_status ensure_ctx(inla_model* m, int count) {
 // the two sets run on two streams.  They are independent until the final
 // combination (the stencil quadratic forms on the Q_p stream wait for x*), so
 // the serial diagonal steps of one set overlap the wide products of the other.
-bta_status record_group(inla_model* m, int mode, int cnt, cudaStream_t s0) {
+bta_status record_group(inla_model* m, int mode, int cnt, int prec, cudaStream_t s0) {
   const ModelDev& md = m->md;
   const int grad = mode >= 1;
   std::vector<SweepItem> ic(cnt), ip(cnt);
@@ -172,6 +182,7 @@ bta_status record_group(inla_model* m, int mode, int cnt, cudaStream_t s0) {
       EvalCtx& c = m->ctx[e];
       BTA_TRY(launch_coef(md, m->L, c.coefbuf, s0));
       BTA_CUDA_TRY(cudaMemsetAsync(c.fail, 0xff, 2 * sizeof(int32_t), s0));
+      BTA_CUDA_TRY(cudaMemsetAsync(c.fail + 2, 0, sizeof(int32_t), s0));
     }
   }
   BTA_CUDA_TRY(cudaEventRecord(m->ev0, s0));
@@ -180,12 +191,23 @@ bta_status record_group(inla_model* m, int mode, int cnt, cudaStream_t s0) {
   if (mode < 2) {
     for (int e = 0; e < cnt; ++e)
       BTA_TRY(launch_assemble(md, m->L, m->ctx[e].coefbuf, 1, m->ctx[e].qc, m->ctx[e].x, m->s1));
-    BTA_TRY(factor_sweep_multi(ic.data(), cnt, m->s1, m->evd));
+    BTA_TRY(factor_sweep_multi(ic.data(), cnt, m->s1, m->evd, prec));
     BTA_TRY(upper_solve_multi(ic.data(), cnt, m->s1));
+    if (prec) {
+      // one step of iterative refinement in FP64: x += Q_c^{-1} (r - Q_c x)
+      for (int e = 0; e < cnt; ++e) {
+        EvalCtx& c = m->ctx[e];
+        BTA_TRY(launch_rhs(md, m->L, c.coefbuf, c.dr, m->s1));
+        BTA_TRY(launch_qc_residual(md, m->L, c.coefbuf, c.x, c.dr, m->s1));
+        BTA_TRY(lower_solve(c.qc, c.dr, c.wsc, m->s1));
+        BTA_TRY(upper_solve(c.qc, c.dr, c.wsc, m->s1));
+        BTA_TRY(launch_axpy((int64_t)md.nt * md.ld + md.a, 1.0, c.dr, c.x, m->s1));
+      }
+    }
     BTA_CUDA_TRY(cudaEventRecord(m->evx, m->s1));
     for (int e = 0; e < cnt; ++e) BTA_TRY(launch_residual(md, m->ctx[e].x, m->ctx[e].RS, m->s1));
   }
-  if (grad) BTA_TRY(selinv_sweep_multi(ic.data(), cnt, m->s1));
+  if (grad) BTA_TRY(selinv_sweep_multi(ic.data(), cnt, m->s1, prec));
   BTA_CUDA_TRY(cudaEventRecord(m->ev1, m->s1));
   // ---- stream 2: Q_p set
   BTA_CUDA_TRY(cudaStreamWaitEvent(m->s2, m->ev0, 0));
@@ -195,12 +217,12 @@ bta_status record_group(inla_model* m, int mode, int cnt, cudaStream_t s0) {
     // start one diagonal step behind the Q_c sweep: the two sweeps then
     // alternate their latency-bound diagonal factors with wide products
     BTA_CUDA_TRY(cudaStreamWaitEvent(m->s2, m->evd, 0));
-    BTA_TRY(factor_sweep_multi(ip.data(), cnt, m->s2));
+    BTA_TRY(factor_sweep_multi(ip.data(), cnt, m->s2, nullptr, prec));
     BTA_CUDA_TRY(cudaStreamWaitEvent(m->s2, m->evx, 0));
     for (int e = 0; e < cnt; ++e)
       BTA_TRY(launch_pattern_quad_all(md, m->ctx[e].x, m->ctx[e].QD, m->ctx[e].QB, m->s2));
   }
-  if (grad) BTA_TRY(selinv_sweep_multi(ip.data(), cnt, m->s2));
+  if (grad) BTA_TRY(selinv_sweep_multi(ip.data(), cnt, m->s2, prec));
   BTA_CUDA_TRY(cudaEventRecord(m->ev2, m->s2));
   // ---- join and combine
   BTA_CUDA_TRY(cudaStreamWaitEvent(s0, m->ev1, 0));
@@ -219,7 +241,8 @@ bta_status record_group(inla_model* m, int mode, int cnt, cudaStream_t s0) {
 
 // Run one group (thetas for contexts 0..cnt-1 already in htheta for mode < 2);
 // outputs land in hout[e * out_size(d)].
-bta_status run_group(inla_model* m, int mode, int cnt, int use_graph, cudaStream_t stream) {
+bta_status run_group(inla_model* m, int mode, int cnt, int prec, int use_graph,
+                     cudaStream_t stream) {
   const int d = m->d, no = out_size(d);
   if (mode < 2)
     for (int e = 0; e < cnt; ++e)
@@ -228,13 +251,13 @@ bta_status run_group(inla_model* m, int mode, int cnt, int use_graph, cudaStream
   if (use_graph) {
     GraphKey* gk = nullptr;
     for (auto& g : m->graphs)
-      if (g.mode == mode && g.count == cnt) gk = &g;
+      if (g.mode == mode && g.count == cnt && g.precision == prec) gk = &g;
     if (!gk) {
       const int64_t before = g_launches;
       cudaStream_t cap;
       BTA_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
       BTA_CUDA_TRY(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-      bta_status st = record_group(m, mode, cnt, cap);
+      bta_status st = record_group(m, mode, cnt, prec, cap);
       cudaGraph_t graph = nullptr;
       cudaError_t e = cudaStreamEndCapture(cap, &graph);
       if (st != BTA_OK) {
@@ -248,14 +271,14 @@ bta_status run_group(inla_model* m, int mode, int cnt, int use_graph, cudaStream
       cudaGraphDestroy(graph);
       cudaStreamDestroy(cap);
       BTA_CUDA_TRY(e);
-      m->graphs.push_back({mode, cnt, exec, g_launches - before});
+      m->graphs.push_back({mode, cnt, prec, exec, g_launches - before});
       gk = &m->graphs.back();
     }
     BTA_CUDA_TRY(cudaGraphLaunch(gk->exec, stream));
     m->launched += gk->kernels;
   } else {
     const int64_t before = g_launches;
-    BTA_TRY(record_group(m, mode, cnt, stream));
+    BTA_TRY(record_group(m, mode, cnt, prec, stream));
     m->launched += g_launches - before;
   }
   for (int e = 0; e < cnt; ++e)
@@ -263,10 +286,17 @@ bta_status run_group(inla_model* m, int mode, int cnt, int use_graph, cudaStream
                                  cudaMemcpyDeviceToHost, stream));
   BTA_CUDA_TRY(cudaStreamSynchronize(stream));
   bta_status st = BTA_OK;
+  if (prec) {
+    for (int e = 0; e < cnt; ++e) {
+      int32_t tcs = 0;
+      BTA_CUDA_TRY(cudaMemcpy(&tcs, m->ctx[e].fail + 2, sizeof(int32_t), cudaMemcpyDeviceToHost));
+      if (tcs != 0) st = BTA_ERR_TIMEOUT;
+    }
+  }
   for (int e = 0; e < cnt; ++e) {
     const double* parts = m->hout + (size_t)e * no + 1 + d;
     if (parts[6] >= 0 || parts[7] >= 0) st = BTA_ERR_NOT_SPD;
-    m->ctx[e].have_factors = mode == 0;
+    m->ctx[e].have_factors = mode == 0 ? 1 + prec : 0;   // remembers the factor's precision
   }
   m->last.assign(m->hout + (size_t)(cnt - 1) * no, m->hout + (size_t)cnt * no);
   return st;
@@ -557,7 +587,8 @@ bta_status bta_selinv(bta_desc* L, inla_model* m, const double* theta, int32_t w
 bta_status inla_value_and_grad(inla_model* m, const double* theta, int32_t batch, double* f,
                                double* grad, const inla_opts* opts, cudaStream_t stream) {
   if (!m || !theta || !f || batch < 1) return BTA_ERR_ARG;
-  if (opts && opts->precision != 0) return BTA_ERR_ARG;
+  const int prec = opts ? opts->precision : 0;
+  if (prec != 0 && prec != 1) return BTA_ERR_ARG;
   for (int i = 0; i < batch; ++i)
     if (!finite_theta(theta + (size_t)i * m->d, m->d)) return BTA_ERR_ARG;
   const int use_graph = opts ? opts->use_graph : 1;
@@ -570,7 +601,7 @@ bta_status inla_value_and_grad(inla_model* m, const double* theta, int32_t batch
   for (int i0 = 0; i0 < batch; i0 += group) {
     const int cnt = std::min(group, batch - i0);
     std::memcpy(m->htheta, theta + (size_t)i0 * d, (size_t)cnt * d * sizeof(double));
-    bta_status s1 = run_group(m, mode, cnt, use_graph, stream);
+    bta_status s1 = run_group(m, mode, cnt, prec, use_graph, stream);
     if (s1 != BTA_OK && s1 != BTA_ERR_NOT_SPD) return s1;
     if (s1 != BTA_OK) st = s1;
     for (int e = 0; e < cnt; ++e) {
@@ -587,7 +618,7 @@ bta_status inla_backward(inla_model* m, double* grad, int32_t use_graph, cudaStr
   if (!m || !grad) return BTA_ERR_ARG;
   if (m->ctx.empty() || !m->ctx[0].have_factors) return BTA_ERR_STATE;
   for (size_t e = 1; e < m->ctx.size(); ++e) m->ctx[e].have_factors = 0;
-  bta_status st = run_group(m, 2, 1, use_graph, stream);
+  bta_status st = run_group(m, 2, 1, m->ctx[0].have_factors - 1, use_graph, stream);
   for (int j = 0; j < m->d; ++j) grad[j] = m->last[1 + j];
   return st;
 }

@@ -222,6 +222,15 @@ bta_status launch_coef(const ModelDev& md, const CoefLayout& L, double* coefbuf,
   return BTA_OK;
 }
 
+bta_status launch_rhs(const ModelDev& md, const CoefLayout& L, const double* coefbuf, double* rhs,
+                      cudaStream_t s) {
+  const int64_t tot = (int64_t)md.nt * md.ld + md.a;
+  assemble_rhs<<<cdiv(tot, 256), 256, 0, s>>>(md.nt, md.ld, md.ns, md.b, md.a, md.a_r,
+                                               coefbuf + L.tau, md.rraw, rhs);
+  BTA_LAUNCHED();
+  return BTA_OK;
+}
+
 bta_status launch_assemble(const ModelDev& md, const CoefLayout& L, const double* coefbuf,
                            int cond, const bta_desc& q, double* rhs, cudaStream_t s) {
   const int ld = md.ld;

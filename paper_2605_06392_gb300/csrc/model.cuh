@@ -81,6 +81,15 @@ bta_status launch_pattern_quad_all(const ModelDev& md, const double* x, double* 
 int resid_chunks(const ModelDev& md);
 bta_status launch_residual(const ModelDev& md, const double* x, double* out, cudaStream_t s);
 
+// Refinement of x*: r <- r - Q_c x in FP64 from the stencil form (no dense
+// blocks: the factor has overwritten them), and y += alpha x.
+bta_status launch_qc_residual(const ModelDev& md, const CoefLayout& L, const double* coefbuf,
+                              const double* x, double* r, cudaStream_t s);
+bta_status launch_axpy(int64_t n, double alpha, const double* x, double* y, cudaStream_t s);
+// r = sum_m tau_m A_m^T y_m alone (n*ld + a).
+bta_status launch_rhs(const ModelDev& md, const CoefLayout& L, const double* coefbuf, double* rhs,
+                      cudaStream_t s);
+
 // Everything the final combination reads.
 struct Reductions {
   const double* PDc;   // [nt][kk][pchunks][kNP]     Z_D of Q_c

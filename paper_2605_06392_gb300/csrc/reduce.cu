@@ -339,4 +339,123 @@ bta_status launch_finalize(const ModelDev& md, const CoefLayout& L, const double
   return BTA_OK;
 }
 
+
+
+// ----------------------------------------------------------------------------
+// FP64 product with Q_c straight from its Kronecker/stencil form (no dense
+// blocks), for the refinement of x* in the mixed-precision mode:
+//   d = r - Q_c x.
+// Block row t of Q_c x:  sum over t' in {t-1, t, t+1} of
+//   sum_q sum_s alpha_{pq,s}(t, t') S_s x_t'^(q)  (+ tau_p cnt x_t on t' = t)
+//   + C_t^T x_T;   tip row:  sum_t C_t x_t + T x_T.
+// The temporal matrices are symmetric, so block (t, t+1) uses B_t's
+// coefficients with p and q exchanged.
+// ----------------------------------------------------------------------------
+namespace {
+
+struct QmvArgs {
+  int k, ns, nt, ld, b, a, a_r, nnz;
+  const int32_t* row_ptr;
+  const int32_t* col;
+  const double* val;
+  const double* alphaD;   // [nt][kk][kNS]
+  const double* alphaB;   // [nt-1][kk][kNS]
+  const double* tau;
+  const double* cnt;
+  const double* craw;     // [nt][a x ld]
+  const double* traw;     // [k][a x a]
+  double tip;
+};
+
+__global__ void qc_residual_lat_kernel(QmvArgs g, const double* __restrict__ x, double* r) {
+  const int t = blockIdx.y;
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= g.ld) return;
+  double* rt = r + (int64_t)t * g.ld;
+  if (row >= g.b) { rt[row] = 0.0; return; }
+  const int p = row / g.ns, s1 = row % g.ns;
+  const int kk = g.k * g.k;
+  double acc = 0.0;
+  const int e0 = g.row_ptr[s1], e1 = g.row_ptr[s1 + 1];
+  for (int dt = -1; dt <= 1; ++dt) {
+    const int u = t + dt;
+    if (u < 0 || u >= g.nt) continue;
+    const double* xu = x + (int64_t)u * g.ld;
+    for (int q = 0; q < g.k; ++q) {
+      const double* al;
+      if (dt == 0) al = g.alphaD + ((int64_t)t * kk + p * g.k + q) * kNS;
+      else if (dt == -1) al = g.alphaB + ((int64_t)u * kk + p * g.k + q) * kNS;   // B_{t-1}
+      else al = g.alphaB + ((int64_t)t * kk + q * g.k + p) * kNS;                  // B_t^T
+      double sq = 0.0;
+      for (int e = e0; e < e1; ++e) {
+        const double w = al[0] * g.val[e] + al[1] * g.val[g.nnz + e] + al[2] * g.val[2 * g.nnz + e];
+        sq = fma(w, xu[q * g.ns + g.col[e]], sq);
+      }
+      acc += sq;
+    }
+  }
+  acc = fma(g.tau[p] * g.cnt[(int64_t)t * g.ld + row], x[(int64_t)t * g.ld + row], acc);
+  if (g.a > 0) {
+    const double* xT = x + (int64_t)g.nt * g.ld;
+    const double* cr = g.craw + (int64_t)t * g.a * g.ld + (int64_t)row * g.a;
+    for (int f = 0; f < g.a; ++f) acc = fma(g.tau[f / g.a_r] * cr[f], xT[f], acc);
+  }
+  rt[row] -= acc;
+}
+
+// Tip rows: one CTA per fixed effect f, deterministic block reduction.
+__global__ void __launch_bounds__(RT) qc_residual_tip_kernel(QmvArgs g, const double* __restrict__ x,
+                                                             double* r) {
+  const int f = blockIdx.x;
+  const double tf = g.tau[f / g.a_r];
+  double v[1] = {0.0};
+  const int64_t tot = (int64_t)g.nt * g.ld;
+  for (int64_t i = threadIdx.x; i < tot; i += RT) {
+    const int t = (int)(i / g.ld), row = (int)(i % g.ld);
+    if (row >= g.b) continue;
+    v[0] = fma(tf * g.craw[(int64_t)t * g.a * g.ld + (int64_t)row * g.a + f], x[i], v[0]);
+  }
+  __shared__ double res[1];
+  block_sum<1>(v, res, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double* xT = x + tot;
+    double acc = res[0];
+    for (int h = 0; h < g.a; ++h) {
+      double th = f == h ? g.tip : 0.0;   // T = tip I + sum_m tau_m traw_m
+      for (int m = 0; m < g.k; ++m) th = fma(g.tau[m], g.traw[(int64_t)m * g.a * g.a + f + h * g.a], th);
+      acc = fma(th, xT[h], acc);
+    }
+    r[tot + f] -= acc;
+  }
+}
+
+__global__ void axpy_kernel(int64_t n, double alpha, const double* __restrict__ x, double* y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = fma(alpha, x[i], y[i]);
+}
+
+}  // namespace
+
+bta_status launch_qc_residual(const ModelDev& md, const CoefLayout& L, const double* coefbuf,
+                              const double* x, double* r, cudaStream_t s) {
+  QmvArgs g{md.k, md.ns, md.nt, md.ld, md.b, md.a, md.a_r, md.nnz, md.row_ptr, md.col, md.val,
+            coefbuf + L.alphaD, coefbuf + L.alphaB, coefbuf + L.tau, md.cnt, md.craw, md.traw,
+            md.tip_prior};
+  qc_residual_lat_kernel<<<dim3(cdiv(md.ld, 128), md.nt), 128, 0, s>>>(g, x, r);
+  BTA_LAUNCHED();
+  if (md.a > 0) {
+    qc_residual_tip_kernel<<<md.a, RT, 0, s>>>(g, x, r);
+    BTA_LAUNCHED();
+  }
+  return BTA_OK;
+}
+
+bta_status launch_axpy(int64_t n, double alpha, const double* x, double* y, cudaStream_t s) {
+  axpy_kernel<<<(int)std::min<int64_t>(cdiv(n, 256), 1216), 256, 0, s>>>(n, alpha, x, y);
+  BTA_LAUNCHED();
+  return BTA_OK;
+}
+
 }  // namespace bta

@@ -235,6 +235,24 @@ inline const double* const* cp(const std::vector<double*>& v) {
   return reinterpret_cast<const double* const*>(v.data());
 }
 
+// A b x b product of the sweep over the items idx: batched FP64, or one
+// split-precision tensor-core product per matrix.
+bta_status big_product(const Gemm& g, const SweepItem* it, const std::vector<int>& idx,
+                       int precision, cudaStream_t s) {
+  if (precision == 0) return gemm_f64(g, s);
+  for (size_t z = 0; z < idx.size(); ++z) {
+    const SweepWs& ws = it[idx[z]].ws;
+    if (!ws.tc) return BTA_ERR_ARG;
+    Gemm one = g;
+    one.batch = 1;
+    one.Ab = nullptr; one.Bb = nullptr; one.Cb = nullptr; one.Cinb = nullptr;
+    one.A = g.Ab[z]; one.B = g.Bb[z]; one.C = g.Cb[z];
+    one.Cin = g.Cinb ? g.Cinb[z] : g.Cb[z];
+    BTA_TRY(tc_gemm_mixed(one, ws.tc, ws.tcstat, s));
+  }
+  return BTA_OK;
+}
+
 bta_status check_set(const SweepItem* it, int m) {
   if (m < 1) return BTA_ERR_ARG;
   for (int z = 0; z < m; ++z) {
@@ -249,7 +267,8 @@ bta_status check_set(const SweepItem* it, int m) {
 // ----------------------------------------------------------------------------
 // Algorithm 1 on a set of matrices
 // ----------------------------------------------------------------------------
-bta_status factor_sweep_multi(const SweepItem* it, int m, cudaStream_t s, cudaEvent_t mark) {
+bta_status factor_sweep_multi(const SweepItem* it, int m, cudaStream_t s, cudaEvent_t mark,
+                              int precision) {
   BTA_TRY(check_set(it, m));
   const int n = it[0].q.n, ld = it[0].q.ld;
   const int64_t blk = (int64_t)ld * ld;
@@ -272,7 +291,7 @@ bta_status factor_sweep_multi(const SweepItem* it, int m, cudaStream_t s, cudaEv
         g.Ab = cp(Bp); g.lda = ld; g.Bb = cp(Bp); g.ldb = ld; g.transB = 1;
         g.Cb = Di.data(); g.ldc = ld; g.Cinb = cp(Di); g.ldcin = ld;
         g.alpha = -1.0; g.beta = 1.0; g.out_lower = 1;
-        BTA_TRY(gemm_f64(g, s));
+        BTA_TRY(big_product(g, it, G.all, precision, s));
       }
       for (const auto& grp : G.arrow) {  // C_i -= L_C,i-1 L_B,i-1^T
         const int a = it[grp[0]].q.a;
@@ -319,7 +338,7 @@ bta_status factor_sweep_multi(const SweepItem* it, int m, cudaStream_t s, cudaEv
       Gemm g; g.M = ld; g.N = ld; g.K = ld; g.batch = M;
       g.Ab = cp(Bi); g.lda = ld; g.Bb = cp(Di); g.ldb = ld; g.transB = 1; g.triB = TRI_UPPER;
       g.Cb = W.data(); g.ldc = ld;
-      BTA_TRY(gemm_f64(g, s));
+      BTA_TRY(big_product(g, it, G.all, precision, s));
       BTA_TRY(copy_block_batch(M, cp(W), ld, Bi.data(), ld, ld, ld, 1.0, 0, s));
     }
     if (!G.vec.empty()) {  // z_i = L_Di^{-1} (r_i - L_B,i-1 z_{i-1});  v_T += L_Ci z_i
@@ -467,7 +486,7 @@ bta_status upper_solve(const bta_desc& q, double* z, const SweepWs& ws, cudaStre
 //   Z_Bi = -Z_D,i+1 F_Bi - Z_C,i+1^T F_Ci
 //   Z_Di = L_Di^{-T} L_Di^{-1} - Z_Bi^T F_Bi - Z_Ci^T F_Ci
 // ----------------------------------------------------------------------------
-bta_status selinv_sweep_multi(const SweepItem* it, int m, cudaStream_t s) {
+bta_status selinv_sweep_multi(const SweepItem* it, int m, cudaStream_t s, int precision) {
   BTA_TRY(check_set(it, m));
   const int n = it[0].q.n, ld = it[0].q.ld;
   const int64_t blk = (int64_t)ld * ld;
@@ -492,7 +511,7 @@ bta_status selinv_sweep_multi(const SweepItem* it, int m, cudaStream_t s) {
       Gemm g; g.M = ld; g.N = ld; g.K = ld; g.batch = M;
       g.Ab = cp(Bi); g.lda = ld; g.Bb = cp(Di); g.ldb = ld; g.triB = TRI_LOWER;
       g.Cb = W1.data(); g.ldc = ld;
-      BTA_TRY(gemm_f64(g, s));
+      BTA_TRY(big_product(g, it, G.all, precision, s));
     }
     for (const auto& grp : G.arrow) {
       const int a = it[grp[0]].q.a, c = (int)grp.size();
@@ -529,7 +548,7 @@ bta_status selinv_sweep_multi(const SweepItem* it, int m, cudaStream_t s) {
         Gemm g; g.M = ld; g.N = ld; g.K = ld; g.batch = M;
         g.Ab = cp(Dn); g.lda = ld; g.Bb = cp(W1); g.ldb = ld;
         g.Cb = W2.data(); g.ldc = ld; g.alpha = -1.0;
-        BTA_TRY(gemm_f64(g, s));
+        BTA_TRY(big_product(g, it, G.all, precision, s));
       }
       for (const auto& grp : G.arrow) {  // W2 -= Z_C,i+1^T F_C
         const int a = it[grp[0]].q.a, c = (int)grp.size();
@@ -548,14 +567,14 @@ bta_status selinv_sweep_multi(const SweepItem* it, int m, cudaStream_t s) {
       g.Ab = cp(Di); g.lda = ld; g.transA = 1; g.triA = TRI_UPPER;
       g.Bb = cp(Di); g.ldb = ld; g.triB = TRI_LOWER;
       g.Cb = W3.data(); g.ldc = ld; g.out_lower = 1;
-      BTA_TRY(gemm_f64(g, s));
+      BTA_TRY(big_product(g, it, G.all, precision, s));
     }
     if (hasB) {  // W3 -= Z_B^T F_B
       Gemm g; g.M = ld; g.N = ld; g.K = ld; g.batch = M;
       g.Ab = cp(W2); g.lda = ld; g.transA = 1; g.Bb = cp(W1); g.ldb = ld;
       g.Cb = W3.data(); g.ldc = ld; g.Cinb = cp(W3); g.ldcin = ld; g.alpha = -1.0; g.beta = 1.0;
       g.out_lower = 1;
-      BTA_TRY(gemm_f64(g, s));
+      BTA_TRY(big_product(g, it, G.all, precision, s));
     }
     for (const auto& grp : G.arrow) {  // W3 -= Z_C^T F_C
       const int a = it[grp[0]].q.a, c = (int)grp.size();

@@ -10,6 +10,10 @@ namespace bta {
 struct SweepWs {
   double *W1 = nullptr, *W2 = nullptr, *W3 = nullptr, *pot = nullptr;
   double *Wc1 = nullptr, *Wc2 = nullptr, *gv = nullptr, *vT = nullptr;
+  // mixed precision only: operand copies of the tensor-core products and
+  // their status word (set by the owner, not by carve)
+  void* tc = nullptr;
+  int32_t* tcstat = nullptr;
   static size_t bytes(int ld, int a);
   void carve(double* base, int ld, int a);
 };
@@ -38,10 +42,13 @@ struct SweepItem {
 };
 // mark (optional): recorded on s right after block 0's diagonal factor, so a
 // concurrent sweep can start one diagonal step behind this one.
+// precision 0: every product in FP64; 1: the b x b off-diagonal Schur
+// products (and the selected-inversion products) in split precision on the
+// tensor cores, the diagonal-block factorisation, arrow and log-det in FP64.
 bta_status factor_sweep_multi(const SweepItem* items, int m, cudaStream_t s,
-                              cudaEvent_t mark = nullptr);
+                              cudaEvent_t mark = nullptr, int precision = 0);
 bta_status upper_solve_multi(const SweepItem* items, int m, cudaStream_t s);
-bta_status selinv_sweep_multi(const SweepItem* items, int m, cudaStream_t s);
+bta_status selinv_sweep_multi(const SweepItem* items, int m, cudaStream_t s, int precision = 0);
 
 bta_status factor_sweep(const bta_desc& q, double* rhs, double* slots, int32_t* fail,
                         const SweepWs& ws, cudaStream_t s);
