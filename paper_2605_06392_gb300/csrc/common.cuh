@@ -104,6 +104,11 @@ struct Gemm {
   const double* const* Bb = nullptr;
   double* const* Cb = nullptr;
   const double* const* Cinb = nullptr;
+  // Optional split-K workspace (per problem, sk_cap doubles each): products
+  // with too few output tiles then run as K chunks plus an ordered sum.
+  double* sk_ws = nullptr;
+  double* const* sk_wsb = nullptr;
+  size_t sk_cap = 0;
 };
 bta_status gemm_f64(const Gemm& g, cudaStream_t s);
 
@@ -148,6 +153,12 @@ bta_status potrf_inv_batch(int count, double* const* A, int n, int ld, double* c
                            double* const* logdet_parts, int32_t* const* fail,
                            const int32_t* fail_code, cudaStream_t s);
 int potrf_inv_slots(int n);   // number of logdet slots potrf_inv writes
+// The task-graph kernel (potrf_dag.cu) used by potrf_inv_batch for n <= 5120;
+// g_potrf_recursive = 1 selects the recursive launch sequence instead.
+bta_status potrf_dag_batch(int count, double* const* A, int n, int ld, double* const* scratch,
+                           double* const* logdet_parts, int32_t* const* fail,
+                           const int32_t* fail_code, cudaStream_t s);
+extern int g_potrf_recursive;
 
 // Small helpers (sweep.cu)
 bta_status copy_block(const double* src, int lds, double* dst, int ldd, int rows, int cols,

@@ -8,6 +8,7 @@
 // BM x BN tile with DFMA from shared-memory stages of BK = 16, prefetching
 // the next stage into registers while the current one is consumed.
 #include <algorithm>
+#include <vector>
 
 #include "common.cuh"
 
@@ -40,6 +41,7 @@ struct GemmDev {
   const double* B[kMaxBatch];
   double* C[kMaxBatch];
   const double* Cin[kMaxBatch];
+  int kb[kMaxBatch], ke[kMaxBatch];   // K range of problem z (split-K chunks)
 };
 
 __device__ __forceinline__ bool a_zero(int tri, int m, int k) {
@@ -65,12 +67,13 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(GemmDev g) {
   double* C = g.C[blockIdx.z];
   const double* Cin = g.Cin[blockIdx.z];
 
-  // K range that can hold nonzeros for this tile.
-  int kbeg = 0, kend = g.K;
+  // K range that can hold nonzeros for this tile (absolute k).
+  int kbeg = g.kb[blockIdx.z], kend = g.ke[blockIdx.z];
   if (g.triA == TRI_LOWER) kend = min(kend, m0 + BM);
   if (g.triA == TRI_UPPER) kbeg = max(kbeg, m0);
   if (g.triB == TRI_LOWER) kbeg = max(kbeg, n0);
   if (g.triB == TRI_UPPER) kend = min(kend, n0 + BN);
+  const int kfirst = kbeg;   // masked loads below start at the chunk start exactly
   kbeg = kbeg / BK * BK;
 
   const int tid = threadIdx.x;
@@ -90,7 +93,7 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(GemmDev g) {
       if (!g.transA) { m = idx % BM; k = idx / BM; } else { k = idx % BK; m = idx / BK; }
       int gm = m0 + m, gk = k0 + k;
       double v = 0.0;
-      if (gm < g.M && gk < kend && !a_zero(g.triA, gm, gk))
+      if (gm < g.M && gk >= kfirst && gk < kend && !a_zero(g.triA, gm, gk))
         v = g.transA ? A[gk + (int64_t)gm * g.lda] : A[gm + (int64_t)gk * g.lda];
       ra[r] = v;
     }
@@ -101,7 +104,7 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(GemmDev g) {
       if (!g.transB) { k = idx % BK; n = idx / BK; } else { n = idx % BN; k = idx / BN; }
       int gn = n0 + n, gk = k0 + k;
       double v = 0.0;
-      if (gn < g.N && gk < kend && !b_zero(g.triB, gk, gn))
+      if (gn < g.N && gk >= kfirst && gk < kend && !b_zero(g.triB, gk, gn))
         v = g.transB ? B[gn + (int64_t)gk * g.ldb] : B[gk + (int64_t)gn * g.ldb];
       rb[r] = v;
     }
@@ -164,6 +167,30 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(GemmDev g) {
 // ----------------------------------------------------------------------------
 // GEMV with a deterministic split over K.
 // ----------------------------------------------------------------------------
+// C_z = alpha * sum_s part_z[s] + beta * Cin_z over an M x N output (fixed
+// order over s, so results do not depend on scheduling).
+struct SplitDev {
+  int M, N, S, ldc, ldcin;
+  double alpha, beta;
+  const double* part[kMaxBatch];
+  double* C[kMaxBatch];
+  const double* Cin[kMaxBatch];
+};
+
+__global__ void splitk_reduce(SplitDev d) {
+  const int z = blockIdx.y;
+  const int64_t mn = (int64_t)d.M * d.N;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < mn;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int m = (int)(e % d.M), n = (int)(e / d.M);
+    double acc = 0.0;
+    for (int s = 0; s < d.S; ++s) acc += d.part[z][(int64_t)s * mn + e];
+    double v = d.alpha * acc;
+    if (d.beta != 0.0) v = fma(d.beta, d.Cin[z][m + (int64_t)n * d.ldcin], v);
+    d.C[z][m + (int64_t)n * d.ldc] = v;
+  }
+}
+
 struct GemvDev {
   int M, K, lda, triA, nsplit;
   double alpha, beta;
@@ -231,12 +258,13 @@ bta_status gemm_f64(const Gemm& g, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return BTA_OK;
   if (g.Ab ? !(g.Bb && g.Cb) : (g.batch != 1 || !g.A || !g.B || !g.C)) return BTA_ERR_ARG;
   const int nb = g.batch;
+  const int K = g.K > 0 ? g.K : 0;
   // Tile choice.  Every tile is FP64-pipe bound and the hardware spreads
   // tiles evenly over the 152 SMs, so an op takes about
   // ceil(tiles / 152) x (BM x BN x K) / rate: pick the shape minimising that
   // (16 x 16 tiles pay ~5 % more for their shared-memory traffic per FMA).
   constexpr int kSMs = 152;
-  auto units = [&](int bm, int bn) -> int64_t {
+  auto units = [&](int bm, int bn, int count) -> int64_t {
     const int tm = cdiv(g.M, bm), tn = cdiv(g.N, bn);
     int64_t u = 0;
     if (!g.out_lower) {
@@ -244,35 +272,73 @@ bta_status gemm_f64(const Gemm& g, cudaStream_t s) {
     } else {
       for (int r = 0; r < tm; ++r) u += std::min(tn, (r * bm + bm - 1) / bn + 1);
     }
-    return u * nb;
+    return u * count;
   };
-  auto cost = [&](int t, double pen) {
-    const int64_t u = units(t, t);
-    return (double)((u + kSMs - 1) / kSMs) * t * t * (1.0 + pen);
-  };
-  int bm = 0;   // 0: 16 x 64 tiles for M <= 16
-  if (g.M > 16) {
+  auto pick = [&](int count) {
+    if (g.M <= 16) return 0;   // 16 x 64 tiles
+    auto cost = [&](int t, double pen) {
+      const int64_t u = units(t, t, count);
+      return (double)((u + kSMs - 1) / kSMs) * t * t * (1.0 + pen);
+    };
     const double c64 = cost(64, 0.0), c32 = cost(32, 0.0), c16 = cost(16, 0.05);
-    bm = 64;
+    int bm = 64;
     double best = c64;
     if (c32 < best) { bm = 32; best = c32; }
     if (c16 < best) { bm = 16; best = c16; }
+    return bm;
+  };
+  // Split-K for products with too few output tiles to fill the GPU (the
+  // skinny arrow products, a x b by b x b): S chunks of K write partial
+  // products to the caller's workspace, then one pass sums them in order.
+  int bm = pick(nb);
+  int S = 1;
+  const bool have_ws = g.sk_ws || g.sk_wsb;
+  if (have_ws && !g.out_lower && K >= 256) {
+    const int bmn = bm == 0 ? 16 : bm, bnn = bm == 0 ? 64 : bm;
+    // decided per problem (not per batch) so that a product gives the same
+    // bits whether it runs alone or inside a batch
+    const int64_t u = units(bmn, bnn, 1);
+    if (u < kSMs) {
+      S = (int)std::min<int64_t>((2 * kSMs + u - 1) / u, std::min(16, K / 64));
+      while (S > 1 && (size_t)S * g.M * g.N > g.sk_cap) --S;
+    }
   }
+  struct Prob { const double *A, *B; double* C; const double* Cin; int kb, ke; };
+  std::vector<Prob> probs;
+  probs.reserve((size_t)nb * S);
+  const int chunk = S > 1 ? (cdiv(K, S) + 15) / 16 * 16 : K;
+  for (int z = 0; z < nb; ++z) {
+    const double* A = g.Ab ? g.Ab[z] : g.A;
+    const double* B = g.Ab ? g.Bb[z] : g.B;
+    double* C = g.Ab ? g.Cb[z] : g.C;
+    const double* Cin = g.Ab ? (g.Cinb ? g.Cinb[z] : g.Cb[z]) : (g.Cin ? g.Cin : g.C);
+    if (S == 1) {
+      probs.push_back({A, B, C, Cin, 0, K});
+    } else {
+      double* ws = g.Ab ? g.sk_wsb[z] : g.sk_ws;
+      for (int c = 0; c < S; ++c) {
+        const int kb = c * chunk, ke = std::min(K, kb + chunk);
+        probs.push_back({A, B, ws + (size_t)c * g.M * g.N, nullptr, kb, std::max(kb, ke)});
+      }
+    }
+  }
+  if (S > 1) bm = pick(nb * S);
   GemmDev d;
-  d.M = g.M; d.N = g.N; d.K = g.K > 0 ? g.K : 0;
+  d.M = g.M; d.N = g.N; d.K = K;
   d.lda = g.lda; d.transA = g.transA; d.triA = g.triA;
   d.ldb = g.ldb; d.transB = g.transB; d.triB = g.triB;
-  d.ldc = g.ldc; d.ldcin = g.Cin || g.Cinb ? g.ldcin : g.ldc;
-  d.alpha = g.alpha; d.beta = g.beta; d.out_lower = g.out_lower;
-  for (int z0 = 0; z0 < nb; z0 += kMaxBatch) {
-    const int cnt = std::min(kMaxBatch, nb - z0);
+  d.ldc = S > 1 ? g.M : g.ldc;
+  d.ldcin = S > 1 ? g.M : (g.Cin || g.Cinb ? g.ldcin : g.ldc);
+  d.alpha = S > 1 ? 1.0 : g.alpha;
+  d.beta = S > 1 ? 0.0 : g.beta;
+  d.out_lower = g.out_lower;
+  const int np = (int)probs.size();
+  for (int z0 = 0; z0 < np; z0 += kMaxBatch) {
+    const int cnt = std::min(kMaxBatch, np - z0);
     for (int z = 0; z < cnt; ++z) {
-      if (!g.Ab) {   // single problem given by the scalar pointers
-        d.A[z] = g.A; d.B[z] = g.B; d.C[z] = g.C; d.Cin[z] = g.Cin ? g.Cin : g.C;
-      } else {
-        d.A[z] = g.Ab[z0 + z]; d.B[z] = g.Bb[z0 + z]; d.C[z] = g.Cb[z0 + z];
-        d.Cin[z] = g.Cinb ? g.Cinb[z0 + z] : g.Cb[z0 + z];
-      }
+      const Prob& q = probs[z0 + z];
+      d.A[z] = q.A; d.B[z] = q.B; d.C[z] = q.C; d.Cin[z] = q.Cin ? q.Cin : q.C;
+      d.kb[z] = q.kb; d.ke[z] = q.ke;
     }
     if (bm == 0) {
       dim3 grid(cdiv(g.M, 16), cdiv(g.N, 64), cnt);
@@ -288,6 +354,25 @@ bta_status gemm_f64(const Gemm& g, cudaStream_t s) {
       launch_prio(gemm_f64_kernel<16, 16>, grid, dim3(NT), s, d);
     }
     BTA_LAUNCHED();
+  }
+  if (S > 1) {
+    SplitDev r;
+    r.M = g.M; r.N = g.N; r.S = S; r.ldc = g.ldc;
+    r.ldcin = g.Cin || g.Cinb ? g.ldcin : g.ldc;
+    r.alpha = g.alpha; r.beta = g.beta;
+    for (int z0 = 0; z0 < nb; z0 += kMaxBatch) {
+      const int cnt = std::min(kMaxBatch, nb - z0);
+      for (int z = 0; z < cnt; ++z) {
+        const int zz = z0 + z;
+        r.part[z] = g.Ab ? g.sk_wsb[zz] : g.sk_ws;
+        r.C[z] = g.Ab ? g.Cb[zz] : g.C;
+        r.Cin[z] = g.Ab ? (g.Cinb ? g.Cinb[zz] : g.Cb[zz]) : (g.Cin ? g.Cin : g.C);
+      }
+      const int64_t mn = (int64_t)g.M * g.N;
+      const int gx = (int)std::min<int64_t>(cdiv(mn, 256), 608);
+      launch_prio(splitk_reduce, dim3(gx, cnt), dim3(256), s, r);
+      BTA_LAUNCHED();
+    }
   }
   return BTA_OK;
 }

@@ -210,11 +210,15 @@ bta_status rec(const PB& b, int64_t aoff, int n, int ld, int64_t woff, int soff,
 
 int potrf_inv_slots(int n) { return n / T; }
 
+int g_potrf_recursive = 0;
+
 bta_status potrf_inv_batch(int count, double* const* A, int n, int ld, double* const* scratch,
                            double* const* logdet_parts, int32_t* const* fail,
                            const int32_t* fail_code, cudaStream_t s) {
   if (n <= 0 || n % T || count < 0) return BTA_ERR_ARG;
   PriorityScope prio(highest_priority());   // the sweep's critical path
+  if (count > 0 && n / T <= 160 && !g_potrf_recursive)
+    return potrf_dag_batch(count, A, n, ld, scratch, logdet_parts, fail, fail_code, s);
   for (int z0 = 0; z0 < count; z0 += kMaxBatch) {
     PB b;
     b.cnt = count - z0 < kMaxBatch ? count - z0 : kMaxBatch;

@@ -298,9 +298,11 @@ bta_status factor_sweep_multi(const SweepItem* it, int m, cudaStream_t s, cudaEv
         auto Cp = ptrs(grp, [&](int z) { return Cb(z, i - 1); });
         auto Bp = ptrs(grp, [&](int z) { return B(z, i - 1); });
         auto Ci = ptrs(grp, [&](int z) { return Cb(z, i); });
+        auto SK = ptrs(grp, [&](int z) { return it[z].ws.W3; });   // W3 is free here
         Gemm g; g.M = a; g.N = ld; g.K = ld; g.batch = (int)grp.size();
         g.Ab = cp(Cp); g.lda = a; g.Bb = cp(Bp); g.ldb = ld; g.transB = 1;
         g.Cb = Ci.data(); g.ldc = a; g.Cinb = cp(Ci); g.ldcin = a; g.alpha = -1.0; g.beta = 1.0;
+        g.sk_wsb = SK.data(); g.sk_cap = blk;
         BTA_TRY(gemm_f64(g, s));
       }
     }
@@ -321,14 +323,17 @@ bta_status factor_sweep_multi(const SweepItem* it, int m, cudaStream_t s, cudaEv
       auto Di = ptrs(grp, [&](int z) { return D(z, i); });
       auto W = ptrs(grp, [&](int z) { return it[z].ws.Wc1; });
       auto T = ptrs(grp, [&](int z) { return it[z].q.T; });
+      auto SK = ptrs(grp, [&](int z) { return it[z].ws.W3; });
       Gemm g; g.M = a; g.N = ld; g.K = ld; g.batch = c;
       g.Ab = cp(Ci); g.lda = a; g.Bb = cp(Di); g.ldb = ld; g.transB = 1; g.triB = TRI_UPPER;
       g.Cb = W.data(); g.ldc = a;
+      g.sk_wsb = SK.data(); g.sk_cap = blk;
       BTA_TRY(gemm_f64(g, s));
       BTA_TRY(copy_block_batch(c, cp(W), a, Ci.data(), a, a, ld, 1.0, 0, s));
       Gemm h; h.M = a; h.N = a; h.K = ld; h.batch = c;
       h.Ab = cp(Ci); h.lda = a; h.Bb = cp(Ci); h.ldb = a; h.transB = 1;
       h.Cb = T.data(); h.ldc = a; h.Cinb = cp(T); h.ldcin = a; h.alpha = -1.0; h.beta = 1.0;
+      h.sk_wsb = SK.data(); h.sk_cap = blk;
       BTA_TRY(gemm_f64(h, s));
     }
     if (i < n - 1) {  // L_Bi = B_i L_Di^{-T}
@@ -520,10 +525,12 @@ bta_status selinv_sweep_multi(const SweepItem* it, int m, cudaStream_t s, int pr
       auto Wc1 = ptrs(grp, [&](int z) { return it[z].ws.Wc1; });
       auto Wc2 = ptrs(grp, [&](int z) { return it[z].ws.Wc2; });
       auto T = ptrs(grp, [&](int z) { return it[z].q.T; });
+      auto SK = ptrs(grp, [&](int z) { return it[z].ws.W3; });   // W3 is free until LAUUM
       {  // Wc1 = F_C = L_Ci L_Di^{-1}
         Gemm g; g.M = a; g.N = ld; g.K = ld; g.batch = c;
         g.Ab = cp(Ci); g.lda = a; g.Bb = cp(Dg); g.ldb = ld; g.triB = TRI_LOWER;
         g.Cb = Wc1.data(); g.ldc = a;
+        g.sk_wsb = SK.data(); g.sk_cap = blk;
         BTA_TRY(gemm_f64(g, s));
       }
       {  // Wc2 = -Z_T F_C
@@ -539,6 +546,7 @@ bta_status selinv_sweep_multi(const SweepItem* it, int m, cudaStream_t s, int pr
         g.Ab = cp(Cn); g.lda = a; g.Bb = cp(W1g); g.ldb = ld;
         g.Cb = Wc2.data(); g.ldc = a; g.Cinb = cp(Wc2); g.ldcin = a; g.alpha = -1.0;
         g.beta = 1.0;
+        g.sk_wsb = SK.data(); g.sk_cap = blk;
         BTA_TRY(gemm_f64(g, s));
       }
     }
