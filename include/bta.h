@@ -211,6 +211,27 @@ bta_status inla_value_and_grad(inla_model* m, const double* theta, int32_t batch
 bta_status inla_backward(inla_model* m, double* grad, int32_t use_graph, cudaStream_t stream);
 
 /*
+ * Several independent models -- e.g. the thetas of a finite-difference
+ * stencil or of a line search on models of different block sizes -- evaluated
+ * by ONE CUDA graph launch: each model's whole evaluation (theta upload,
+ * both factorisations, solve, optional selected inversions, result download)
+ * is a branch of the graph on that model's own streams, so the branches of
+ * uneven size run concurrently and fill each other's idle SMs.
+ *   inla_batch_create: the models (distinct, each used by at most one batch
+ *     at a time) are borrowed, not copied.
+ *   inla_batch_value_and_grad: theta row i (host, leading dimension ldt >=
+ *     every model's d) goes to model i; f[i], grad row i (ldt stride, or
+ *     grad = NULL for values only).  opts->precision as for
+ *     inla_value_and_grad.  The graph is captured on the first call per
+ *     (value/gradient, precision) and replayed after.  Synchronises stream.
+ */
+typedef struct inla_batch inla_batch;
+bta_status inla_batch_create(inla_model* const* models, int32_t count, inla_batch** out);
+void inla_batch_destroy(inla_batch* b);
+bta_status inla_batch_value_and_grad(inla_batch* b, const double* theta, int32_t ldt, double* f,
+                                     double* grad, const inla_opts* opts, cudaStream_t stream);
+
+/*
  * inla_last_parts -- diagnostics of the last single evaluation (host):
  * parts[0..7] = log|Q_p|, log|Q_c|, x^T Q_p x, log l, log p, f, (unused) x2;
  * phases (may be NULL): 4 x d values Phase A, Phase B, Phase C, explicit.

@@ -67,6 +67,11 @@ SIGNATURES = {
                                       C.POINTER(C.c_double), C.POINTER(C.c_double),
                                       C.POINTER(inla_opts), C.c_void_p]),
     "inla_backward": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_int32, C.c_void_p]),
+    "inla_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)]),
+    "inla_batch_destroy": (None, [C.c_void_p]),
+    "inla_batch_value_and_grad": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_int32,
+                                            C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                            C.POINTER(inla_opts), C.c_void_p]),
     "inla_last_parts": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "inla_copy_mode": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "inla_kernel_launches": (C.c_int64, [C.c_void_p]),

@@ -15,7 +15,7 @@ import torch
 from . import _capi
 from ._capi import bta_desc, check, inla_model_spec, inla_opts, lib
 
-__all__ = ["InlaModel", "BtaMatrix", "bta_assemble", "bta_factor", "bta_solve", "bta_selinv",
+__all__ = ["InlaModel", "InlaBatch", "BtaMatrix", "bta_assemble", "bta_factor", "bta_solve", "bta_selinv",
            "inla_value_and_grad", "grid_stencil", "theta_dim", "bta_gemm"]
 
 
@@ -239,3 +239,45 @@ def bta_gemm(A: torch.Tensor, B: torch.Tensor, C_out: torch.Tensor, alpha: float
                          C.c_void_p(B.data_ptr()), B.shape[1], int(transB), beta,
                          C.c_void_p(C_out.data_ptr()), C_out.shape[1], _stream(stream)),
           "bta_gemm")
+
+
+class InlaBatch:
+    """Several models evaluated by one CUDA graph launch
+    (inla_batch_value_and_grad): each model's whole evaluation is a branch of
+    the graph, so models of uneven block size run concurrently."""
+
+    def __init__(self, models):
+        self.models = list(models)
+        arr = (C.c_void_p * len(self.models))(*[m.handle.value for m in self.models])
+        h = C.c_void_p()
+        check(lib().inla_batch_create(arr, len(self.models), C.byref(h)), "inla_batch_create")
+        self.handle = h
+        self.ldt = max(m.d for m in self.models)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().inla_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def value_and_grad(self, thetas, grad: bool = True, precision: int = 0, stream=None):
+        n = len(self.models)
+        th = np.zeros((n, self.ldt))
+        for i, t in enumerate(thetas):
+            th[i, :len(t)] = t
+        f = np.zeros(n)
+        g = np.zeros((n, self.ldt)) if grad else None
+        opts = inla_opts(precision=int(precision), use_graph=1, streams=1, reserved=0)
+        dp = C.POINTER(C.c_double)
+        check(lib().inla_batch_value_and_grad(self.handle, th.ctypes.data_as(dp), self.ldt,
+                                              f.ctypes.data_as(dp),
+                                              g.ctypes.data_as(dp) if grad else None,
+                                              C.byref(opts), _stream(stream)),
+              "inla_batch_value_and_grad")
+        grads = [g[i, :m.d].copy() for i, m in enumerate(self.models)] if grad else None
+        return f, grads

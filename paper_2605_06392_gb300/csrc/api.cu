@@ -61,7 +61,17 @@ struct inla_model {
   int64_t launched = 0;         // kernels this model ran (graph replays included)
   // the Q_c set and the Q_p set are swept on two streams (fork/join by events)
   cudaStream_t s1 = nullptr, s2 = nullptr;
+  cudaStream_t s0 = nullptr;    // the model's own root stream inside a multi-model graph
   cudaEvent_t ev0 = nullptr, evx = nullptr, ev1 = nullptr, ev2 = nullptr, evd = nullptr;
+  cudaEvent_t evj = nullptr;    // join event of a multi-model graph
+};
+
+// Several models evaluated by one CUDA graph (see inla_batch_value_and_grad).
+struct inla_batch {
+  std::vector<inla_model*> models;
+  cudaGraphExec_t exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [grad][precision]
+  int64_t kernels[2][2] = {{0, 0}, {0, 0}};
+  cudaEvent_t fork = nullptr;
 };
 
 namespace {
@@ -329,7 +339,8 @@ void inla_model_destroy(inla_model* m) {
   if (m->htheta) cudaFreeHost(m->htheta);
   if (m->s1) cudaStreamDestroy(m->s1);
   if (m->s2) cudaStreamDestroy(m->s2);
-  for (cudaEvent_t e : {m->ev0, m->evx, m->ev1, m->ev2, m->evd})
+  if (m->s0) cudaStreamDestroy(m->s0);
+  for (cudaEvent_t e : {m->ev0, m->evx, m->ev1, m->ev2, m->evd, m->evj})
     if (e) cudaEventDestroy(e);
   delete m;
 }
@@ -419,7 +430,8 @@ static bta_status model_create_impl(const inla_model_spec* sp, inla_model* m) {
   BTA_CUDA_TRY(cudaMallocHost(&m->htheta, (size_t)kMaxBatch * kMaxD * sizeof(double)));
   BTA_CUDA_TRY(cudaStreamCreateWithFlags(&m->s1, cudaStreamNonBlocking));
   BTA_CUDA_TRY(cudaStreamCreateWithFlags(&m->s2, cudaStreamNonBlocking));
-  for (cudaEvent_t* e : {&m->ev0, &m->evx, &m->ev1, &m->ev2, &m->evd})
+  BTA_CUDA_TRY(cudaStreamCreateWithFlags(&m->s0, cudaStreamNonBlocking));
+  for (cudaEvent_t* e : {&m->ev0, &m->evx, &m->ev1, &m->ev2, &m->evd, &m->evj})
     BTA_CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
   BTA_CUDA_TRY(cudaDeviceSynchronize());
   return BTA_OK;
@@ -649,6 +661,102 @@ bta_status bta_gemm_mixed(int32_t M, int32_t N, int32_t K, double alpha, const d
   BTA_CUDA_TRY(cudaMallocAsync(&ws, tc_gemm_ws_bytes(M, N, K), stream));
   bta_status st = tc_gemm_mixed(g, ws, status, stream);
   cudaFreeAsync(ws, stream);
+  return st;
+}
+
+bta_status inla_batch_create(inla_model* const* models, int32_t count, inla_batch** out) {
+  if (!models || !out || count < 1) return BTA_ERR_ARG;
+  *out = nullptr;
+  inla_batch* b = new (std::nothrow) inla_batch();
+  if (!b) return BTA_ERR_NOMEM;
+  for (int i = 0; i < count; ++i) {
+    if (!models[i]) { delete b; return BTA_ERR_ARG; }
+    for (int j = 0; j < i; ++j)
+      if (models[j] == models[i]) { delete b; return BTA_ERR_ARG; }
+    b->models.push_back(models[i]);
+  }
+  if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess) {
+    delete b;
+    return BTA_ERR_CUDA;
+  }
+  *out = b;
+  return BTA_OK;
+}
+
+void inla_batch_destroy(inla_batch* b) {
+  if (!b) return;
+  cudaDeviceSynchronize();
+  for (auto& row : b->exec)
+    for (auto& e : row)
+      if (e) cudaGraphExecDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  delete b;
+}
+
+// Record every model's evaluation (theta upload, sweeps, result download)
+// as branches forked from s0.
+static bta_status record_batch(inla_batch* b, int grad, int prec, cudaStream_t s0) {
+  BTA_CUDA_TRY(cudaEventRecord(b->fork, s0));
+  for (inla_model* m : b->models) {
+    BTA_CUDA_TRY(cudaStreamWaitEvent(m->s0, b->fork, 0));
+    BTA_CUDA_TRY(cudaMemcpyAsync(m->ctx[0].coefbuf + m->L.theta, m->htheta,
+                                 m->d * sizeof(double), cudaMemcpyHostToDevice, m->s0));
+    BTA_TRY(record_group(m, grad, 1, prec, m->s0));
+    BTA_CUDA_TRY(cudaMemcpyAsync(m->hout, m->ctx[0].out, out_size(m->d) * sizeof(double),
+                                 cudaMemcpyDeviceToHost, m->s0));
+    BTA_CUDA_TRY(cudaEventRecord(m->evj, m->s0));
+    BTA_CUDA_TRY(cudaStreamWaitEvent(s0, m->evj, 0));
+  }
+  return BTA_OK;
+}
+
+bta_status inla_batch_value_and_grad(inla_batch* b, const double* theta, int32_t ldt, double* f,
+                                     double* grad, const inla_opts* opts, cudaStream_t stream) {
+  if (!b || !theta || !f || ldt < 1) return BTA_ERR_ARG;
+  const int prec = opts ? opts->precision : 0;
+  if (prec != 0 && prec != 1) return BTA_ERR_ARG;
+  const int g = grad ? 1 : 0;
+  const int nm = (int)b->models.size();
+  for (int i = 0; i < nm; ++i) {
+    inla_model* m = b->models[i];
+    if (m->d > ldt || !finite_theta(theta + (size_t)i * ldt, m->d)) return BTA_ERR_ARG;
+    std::memcpy(m->htheta, theta + (size_t)i * ldt, m->d * sizeof(double));
+  }
+  if (!b->exec[g][prec]) {
+    const int64_t before = g_launches;
+    cudaStream_t cap;
+    BTA_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    BTA_CUDA_TRY(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    bta_status st = record_batch(b, g, prec, cap);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(cap, &graph);
+    if (st != BTA_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaStreamDestroy(cap);
+      return st;
+    }
+    BTA_CUDA_TRY(e);
+    e = cudaGraphInstantiate(&b->exec[g][prec], graph, 0);
+    cudaGraphDestroy(graph);
+    cudaStreamDestroy(cap);
+    BTA_CUDA_TRY(e);
+    b->kernels[g][prec] = g_launches - before;
+  }
+  BTA_CUDA_TRY(cudaGraphLaunch(b->exec[g][prec], stream));
+  BTA_CUDA_TRY(cudaStreamSynchronize(stream));
+  bta_status st = BTA_OK;
+  for (int i = 0; i < nm; ++i) {
+    inla_model* m = b->models[i];
+    const int no = out_size(m->d);
+    m->last.assign(m->hout, m->hout + no);
+    m->ctx[0].have_factors = g ? 0 : 1 + prec;
+    m->launched += b->kernels[g][prec] / nm;
+    f[i] = m->hout[0];
+    if (grad)
+      for (int j = 0; j < m->d; ++j) grad[(size_t)i * ldt + j] = m->hout[1 + j];
+    const double* parts = m->hout + 1 + m->d;
+    if (parts[6] >= 0 || parts[7] >= 0) st = BTA_ERR_NOT_SPD;
+  }
   return st;
 }
 

@@ -294,7 +294,9 @@ bta_status gemm_f64(const Gemm& g, cudaStream_t s) {
   int S = 1;
   const bool have_ws = g.sk_ws || g.sk_wsb;
   if (have_ws && !g.out_lower && K >= 256) {
-    const int bmn = bm == 0 ? 16 : bm, bnn = bm == 0 ? 64 : bm;
+    // a fixed reference tile (not the chosen one): the split, and so the
+    // bits of the result, never depend on tile selection
+    const int bmn = g.M <= 16 ? 16 : 32, bnn = g.M <= 16 ? 64 : 32;
     // decided per problem (not per batch) so that a product gives the same
     // bits whether it runs alone or inside a batch
     const int64_t u = units(bmn, bnn, 1);

@@ -277,3 +277,26 @@ def test_multi_tile_block_1024(P, name):
     o = _oracle(prob)
     assert abs(f - o.f) <= RTOL * abs(o.f)
     assert np.max(np.abs(g - o.grad) / _grad_scale(o)) <= RTOL
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_multi_model_single_graph_batch(P, precision):
+    # models of uneven block size (b = 64, 120, 48 -> ld 64, 128, 64) in one graph
+    probs = [workloads.make_problem("st_tiny"),
+             workloads.make_problem("st_tiny", nx=12, ny=10, nt=3, n_obs=600, seed=9),
+             workloads.make_problem("coreg_tiny")]
+    models = [P.InlaModel(p) for p in probs]
+    singles = [m.value_and_grad(p.theta, precision=precision) for m, p in zip(models, probs)]
+    batch = P.InlaBatch(models)
+    for _ in range(2):    # captured on the first call, replayed on the second
+        f, g = batch.value_and_grad([p.theta for p in probs], precision=precision)
+        for i in range(len(probs)):
+            assert f[i] == singles[i][0]
+            np.testing.assert_array_equal(g[i], singles[i][1])
+    fv, _ = batch.value_and_grad([p.theta for p in probs], grad=False, precision=precision)
+    np.testing.assert_array_equal(fv, f)
+    if precision == 0:
+        for i, p in enumerate(probs):
+            o = _oracle(p)
+            assert abs(f[i] - o.f) <= RTOL * abs(o.f)
+    batch.close()
