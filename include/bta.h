@@ -211,6 +211,19 @@ bta_status inla_value_and_grad(inla_model* m, const double* theta, int32_t batch
 bta_status inla_backward(inla_model* m, double* grad, int32_t use_graph, cudaStream_t stream);
 
 /*
+ * inla_hessian -- Section III-D, Eq. 13: the posterior Hessian at theta as
+ * central differences of exact gradients, H[:, j] = (grad f(theta + h e_j) -
+ * grad f(theta - h e_j)) / 2h, i.e. 2d + 1 calls of the gradient instead of
+ * 2d^2 + 1 objective evaluations (the paper uses h = 5e-3).  H: host, d x d
+ * row-major (H[i*d + j] = dgrad_i / dtheta_j, not symmetrised); grad0: host,
+ * d values of the gradient at theta, or NULL.  opts as for
+ * inla_value_and_grad (opts->streams > 1 evaluates that many gradients
+ * together).  Synchronises stream.
+ */
+bta_status inla_hessian(inla_model* m, const double* theta, double h, double* H, double* grad0,
+                        const inla_opts* opts, cudaStream_t stream);
+
+/*
  * Several independent models -- e.g. the thetas of a finite-difference
  * stencil or of a line search on models of different block sizes -- evaluated
  * by ONE CUDA graph launch: each model's whole evaluation (theta upload,

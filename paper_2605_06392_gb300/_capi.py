@@ -72,6 +72,9 @@ SIGNATURES = {
     "inla_batch_value_and_grad": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_int32,
                                             C.POINTER(C.c_double), C.POINTER(C.c_double),
                                             C.POINTER(inla_opts), C.c_void_p]),
+    "inla_hessian": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_double,
+                               C.POINTER(C.c_double), C.POINTER(C.c_double),
+                               C.POINTER(inla_opts), C.c_void_p]),
     "inla_last_parts": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "inla_copy_mode": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "inla_kernel_launches": (C.c_int64, [C.c_void_p]),

@@ -760,6 +760,31 @@ bta_status inla_batch_value_and_grad(inla_batch* b, const double* theta, int32_t
   return st;
 }
 
+bta_status inla_hessian(inla_model* m, const double* theta, double h, double* H, double* grad0,
+                        const inla_opts* opts, cudaStream_t stream) {
+  if (!m || !theta || !H || !(h > 0.0) || !finite_theta(theta, m->d)) return BTA_ERR_ARG;
+  const int d = m->d;
+  // rows: theta, then theta + h e_j, theta - h e_j for every j (Eq. 13)
+  std::vector<double> pts((size_t)(2 * d + 1) * d), f(2 * d + 1), g((size_t)(2 * d + 1) * d);
+  for (int r = 0; r < 2 * d + 1; ++r)
+    for (int j = 0; j < d; ++j) pts[(size_t)r * d + j] = theta[j];
+  for (int j = 0; j < d; ++j) {
+    pts[(size_t)(1 + 2 * j) * d + j] += h;
+    pts[(size_t)(2 + 2 * j) * d + j] -= h;
+  }
+  inla_opts o = opts ? *opts : inla_opts{0, 1, 1, 0};
+  if (o.streams < 1) o.streams = 1;
+  bta_status st = inla_value_and_grad(m, pts.data(), 2 * d + 1, f.data(), g.data(), &o, stream);
+  if (st != BTA_OK) return st;
+  for (int j = 0; j < d; ++j)
+    for (int i = 0; i < d; ++i)   // column j: central difference of the gradient along e_j
+      H[(size_t)i * d + j] = (g[(size_t)(1 + 2 * j) * d + i] - g[(size_t)(2 + 2 * j) * d + i]) /
+                             (2.0 * h);
+  if (grad0)
+    for (int i = 0; i < d; ++i) grad0[i] = g[i];
+  return BTA_OK;
+}
+
 bta_status inla_last_parts(const inla_model* m, double* parts, double* phases) {
   if (!m || m->last.empty()) return BTA_ERR_STATE;
   const double* p = m->last.data() + 1 + m->d;
