@@ -141,21 +141,33 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def gemm_roofline(P, torch, b, reps=5):
-    """Average duration of the FP64 tile GEMM at the sweep's dense block
-    shape (b x b x b, the Z_B = -Z_D,i+1 F_B product of the selected
-    inversion), timed with CUDA events on its launch stream."""
+def gemm_roofline(P, torch, b, reps=5, mixed=False):
+    """Average duration of the FP64 tile GEMM (or, mixed=True, of the
+    split-TF32 tensor-core GEMM with its operand splitting) at the sweep's
+    dense block shape (b x b x b, the Z_B = -Z_D,i+1 F_B product of the
+    selected inversion), timed with CUDA events on its launch stream."""
+    import ctypes as C
+    from paper_2605_06392_gb300._capi import lib
     A = torch.randn(b, b, dtype=torch.float64, device="cuda")
     B = torch.randn(b, b, dtype=torch.float64, device="cuda")
     Cm = torch.zeros(b, b, dtype=torch.float64, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
     s = torch.cuda.current_stream()
+
+    def one():
+        if not mixed:
+            P.bta_gemm(A, B, Cm, stream=s)
+        else:
+            lib().bta_gemm_mixed(b, b, b, 1.0, C.c_void_p(A.data_ptr()), b, 0,
+                                 C.c_void_p(B.data_ptr()), b, 0, 0.0, C.c_void_p(Cm.data_ptr()),
+                                 b, C.c_void_p(st.data_ptr()), C.c_void_p(s.cuda_stream))
     for _ in range(2):
-        P.bta_gemm(A, B, Cm, stream=s)
+        one()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(s)
     for _ in range(reps):
-        P.bta_gemm(A, B, Cm, stream=s)
+        one()
     e1.record(s)
     e1.synchronize()
     ms = e0.elapsed_time(e1) / reps
@@ -246,9 +258,10 @@ def main():
         return run_batch(args, P, torch, workloads)
     if args.mode == "gemm":
         b = workloads.WORKLOADS[WORKLOAD]["nx"] * workloads.WORKLOADS[WORKLOAD]["ny"]
-        ms, tf = gemm_roofline(P, torch, b, reps=args.steps)
-        print(json.dumps({"kernel": "gemm_f64_kernel", "shape": [b, b, b], "launch_ms": ms,
-                          "tflops": tf, "frac": tf / FP64_PEAK_TFLOPS}), flush=True)
+        ms, tf = gemm_roofline(P, torch, b, reps=args.steps, mixed=bool(args.precision))
+        name = "tc_gemm_tf32x3_kernel (+ split)" if args.precision else "gemm_f64_kernel"
+        print(json.dumps({"kernel": name, "shape": [b, b, b], "launch_ms": ms,
+                          "tflops_fp64_equivalent": tf}), flush=True)
         return
 
     prob = workloads.make_problem(WORKLOAD, **({"nt": args.nt} if args.nt else {}))
