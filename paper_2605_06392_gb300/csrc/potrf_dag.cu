@@ -25,6 +25,7 @@
 // block's failure word and returns, and every other CTA returns at its next
 // wait.
 #include <algorithm>
+#include <cstdlib>
 #include <vector>
 
 #include "common.cuh"
@@ -38,7 +39,7 @@ constexpr int kMaxP = 160;              // tile rows supported (ld <= 5120)
 constexpr unsigned long long kWaitNs = 2000000000ull;
 constexpr int32_t kFailTimeout = 0x40000000;
 
-enum : int { TK_F = 0, TK_S = 1, TK_G = 2, TK_U = 3, TK_V = 4 };
+enum : int { TK_F = 0, TK_S = 1, TK_G = 2, TK_U = 3, TK_V = 4, TK_C = 5 };
 
 struct DagInst {
   double* A;       // n x n block, ld
@@ -54,6 +55,8 @@ struct DagArgs {
   int total;                // tasks over all instances
   int* counter;             // global task ticket
   int* abort;               // shared abort flag
+  int* smbusy;              // per SM: chain tasks running there (see TK_C)
+  int yield;                // bulk tasks wait while a chain task holds their SM
   int off[kMaxP + 1];       // task offset of each step within one instance
   DagInst inst[kMaxBatch];
 };
@@ -65,6 +68,11 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
 }
 __device__ __forceinline__ void st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int sm_id() {
+  int v;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(v));
+  return v;
 }
 __device__ __forceinline__ unsigned long long now_ns() {
   unsigned long long t;
@@ -134,9 +142,24 @@ struct Task {
   int type, i, j, k;
 };
 
-// Decode task index l of one instance (see the list order above).
+// Number of tasks of step k (see potrf_dag_batch for the list order).
+__host__ __device__ inline int step_tasks(int p, int k) {
+  const int nS = p - 2 - k > 0 ? p - 2 - k : 0;
+  const int nC = k + 1 < p ? 1 : 0;
+  const int nU = (p - 1 - k) * (p - k) / 2 - nC;
+  const int nV = (p - 1 - k) * (k + 1);
+  return nS + nC + k + nU + nV;
+}
+
+// Decode task index l of one instance.  Index 0 is F(0); then for each step
+// k: S(i,k) for i >= k+2, the fused chain task C(k+1) = S(k+1,k) +
+// U(k+1,k+1,k) + F(k+1), G(k,j), the remaining U(i,j,k) (column k+1 first),
+// and V(i,j,k).
 __device__ Task decode(const DagArgs& g, int l) {
   const int p = g.p;
+  Task t{TK_F, 0, 0, 0};
+  if (l == 0) return t;
+  l -= 1;
   int lo = 0, hi = p - 1;
   while (lo < hi) {   // largest k with off[k] <= l
     const int mid = (lo + hi + 1) >> 1;
@@ -144,25 +167,42 @@ __device__ Task decode(const DagArgs& g, int l) {
   }
   const int k = lo;
   int r = l - g.off[k];
-  Task t{0, 0, 0, k};
-  if (r == 0) { t.type = TK_F; t.i = k; t.j = k; return t; }
-  r -= 1;
-  const int nS = p - 1 - k;
-  if (r < nS) { t.type = TK_S; t.i = k + 1 + r; t.j = k; return t; }
+  t.k = k;
+  const int nS = p - 2 - k > 0 ? p - 2 - k : 0;
+  if (r < nS) { t.type = TK_S; t.i = k + 2 + r; t.j = k; return t; }
   r -= nS;
+  if (k + 1 < p) {
+    if (r == 0) { t.type = TK_C; t.i = k + 1; t.j = k + 1; return t; }
+    r -= 1;
+  }
   if (r < k) { t.type = TK_G; t.i = k; t.j = r; return t; }
   r -= k;
-  const int nU = (p - 1 - k) * (p - k) / 2;
-  if (r < nU) {   // columns j = k+1.. in order, rows i = j..p-1
+  const int nU = (p - 1 - k) * (p - k) / 2 - (k + 1 < p ? 1 : 0);
+  if (r < nU) {   // columns j = k+1.. in order, rows i = j..p-1, skipping (k+1, k+1)
     int j = k + 1;
-    while (r >= p - j) { r -= p - j; ++j; }
-    t.type = TK_U; t.j = j; t.i = j + r; return t;
+    int len = p - j - 1;            // column k+1 without its diagonal tile
+    while (r >= len) { r -= len; ++j; len = p - j; }
+    t.type = TK_U; t.j = j; t.i = (j == k + 1 ? j + 1 : j) + r; return t;
   }
   r -= nU;
   t.type = TK_V;   // rows i = k+1.. in order, columns j = 0..k
   t.i = k + 1 + r / (k + 1);
   t.j = r % (k + 1);
   return t;
+}
+
+// 1 / v by Newton-Raphson (r <- r + r (1 - v r), each step doubling the
+// correct bits) from the FP32 reciprocal: two steps reach FP64 accuracy with
+// 4 dependent FP64 operations, where a division costs about ten on the
+// leaf's serial chain.  Values outside FP32's range use the division.
+__device__ __forceinline__ double recip(double v) {
+  const double av = fabs(v);
+  if (!(av > 1e-30 && av < 1e30)) return 1.0 / v;
+  double r = (double)__frcp_rn((float)v);
+  double e = fma(-v, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-v, r, 1.0);
+  return fma(r, e, r);
 }
 
 // Leaf on smem tile S (lower, W_kk): writes X_kk = L_kk^{-1} into Xo, returns
@@ -188,7 +228,7 @@ __device__ void leaf(double (*S)[T + 1], double (*X)[T + 1], double* lcol, doubl
     }
   }
   for (int e = tid; e < T * T; e += kDagThreads) X[e % T][e / T] = (e % T == e / T) ? 1.0 : 0.0;
-  if (tid == 0) rinv[0] = 1.0 / S[0][0];
+  if (tid == 0) rinv[0] = recip(S[0][0]);
   __syncthreads();
   for (int j = 0; j < T; ++j) {
     if (tid > j && tid < T) lcol[tid] = S[tid][j] * rinv[j];
@@ -201,7 +241,7 @@ __device__ void leaf(double (*S)[T + 1], double (*X)[T + 1], double* lcol, doubl
         if (k > j) {
           const double v = fma(-lij, S[k][j], S[i][k]);
           S[i][k] = v;
-          if (i == j + 1 && k == j + 1) rinv[j + 1] = 1.0 / v;
+          if (i == j + 1 && k == j + 1) rinv[j + 1] = recip(v);
         } else {
           X[i][k] = fma(-lij, X[j][k], X[i][k]);
         }
@@ -231,7 +271,7 @@ __device__ void leaf(double (*S)[T + 1], double (*X)[T + 1], double* lcol, doubl
 }
 
 __global__ void __launch_bounds__(kDagThreads) potrf_dag_kernel(DagArgs g) {
-  __shared__ double S0[T][T + 1], S1[T][T + 1], S2[T][T + 1];
+  __shared__ double S0[T][T + 1], S1[T][T + 1], S2[T][T + 1], S3[T][T + 1];
   __shared__ double lcol[T], rinv[T];
   __shared__ int s_task, s_ok;
   __shared__ double s_logdet;
@@ -257,6 +297,11 @@ __global__ void __launch_bounds__(kDagThreads) potrf_dag_kernel(DagArgs g) {
       bool ok = true;
       switch (t.type) {
         case TK_F: ok = wait_ge(&cntW[t.k * p + t.k], t.k, g.abort); break;
+        case TK_C:   // t.i = k + 1 = c: W_{c,c-1} and W_cc up to step c-2 here;
+                     // F(c-1) is awaited after these tiles are loaded
+          ok = wait_ge(&cntW[t.i * p + t.i - 1], t.i - 1, g.abort) &&
+               wait_ge(&cntW[t.i * p + t.i], t.i - 1, g.abort);
+          break;
         case TK_S:
           ok = wait_ge(&doneF[t.k], 1, g.abort) && wait_ge(&cntW[t.i * p + t.k], t.k, g.abort);
           break;
@@ -275,6 +320,20 @@ __global__ void __launch_bounds__(kDagThreads) potrf_dag_kernel(DagArgs g) {
                            : wait_ge(&doneG[t.k * p + t.j], 1, g.abort)) &&
                wait_ge(&cntR[t.i * p + t.j], t.k - t.j, g.abort);
       }
+      // A bulk task starts only when no chain task holds this SM, so the chain
+      // (the latency-critical path) gets the SM's whole FP64 pipe.
+      if (ok && g.yield && t.type != TK_C && t.type != TK_F) {
+        const int* busy = &g.smbusy[sm_id() & 255];
+        if (ld_acquire(busy) > 0) {
+          const unsigned long long t0 = now_ns();
+          while (ld_acquire(busy) > 0) {
+            __nanosleep(128);
+            if (ld_acquire(g.abort)) { ok = false; break; }
+            if (now_ns() - t0 > kWaitNs) { atomicExch(g.abort, 1); ok = false; break; }
+          }
+        }
+      }
+      if (ok && t.type == TK_C && g.yield) atomicAdd(&g.smbusy[sm_id() & 255], 1);
       s_ok = ok;
       if (!ok) atomicCAS(I.fail, -1, kFailTimeout);
     }
@@ -293,6 +352,46 @@ __global__ void __launch_bounds__(kDagThreads) potrf_dag_kernel(DagArgs g) {
         }
         __syncthreads();
         if (threadIdx.x == 0) { __threadfence(); st_release(&doneF[t.k], 1); }
+        break;
+      }
+      case TK_C: {   // c = t.i: L_{c,c-1}, W_cc -= L L^T, then the leaf of W_cc
+        const int c = t.i;
+        load_tile(S0, tile(I.A, ld, c, c - 1), ld);
+        load_tile(S3, tile(I.A, ld, c, c), ld);
+        if (threadIdx.x == 0) s_ok = wait_ge(&doneF[c - 1], 1, g.abort);
+        __syncthreads();
+        if (!s_ok) {
+          if (threadIdx.x == 0) {
+            atomicCAS(I.fail, -1, kFailTimeout);
+            if (g.yield) atomicSub(&g.smbusy[sm_id() & 255], 1);
+          }
+          return;
+        }
+        load_tile(S1, tile(I.A, ld, c - 1, c - 1), ld);
+        __syncthreads();
+        for (int e = threadIdx.x; e < T * T; e += kDagThreads)
+          if (e % T < e / T) S1[e % T][e / T] = 0.0;
+        __syncthreads();
+        tile_mm(S0, S1, true, S2, 1.0, false);            // S2 = L_{c,c-1}
+        __syncthreads();
+        store_tile(Lt(c, c - 1), T, S2, false);
+        __syncthreads();
+        if (threadIdx.x == 0) { __threadfence(); st_release(&doneS[c * p + c - 1], 1); }
+        tile_mm(S2, S2, true, S3, -1.0, true);            // W_cc -= L L^T
+        __syncthreads();
+        leaf(S3, S1, lcol, rinv, &s_logdet, &s_bad);
+        store_tile(tile(I.A, ld, c, c), ld, S1, true);
+        if (threadIdx.x == 0) {
+          I.slots[c] = s_logdet;
+          if (s_bad) atomicCAS(I.fail, -1, I.code);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          __threadfence();
+          st_release(&cntW[c * p + c], c);
+          st_release(&doneF[c], 1);
+          if (g.yield) atomicSub(&g.smbusy[sm_id() & 255], 1);
+        }
         break;
       }
       case TK_S: {   // L_ik = W_ik X_kk^T
@@ -361,16 +460,36 @@ __global__ void __launch_bounds__(kDagThreads) potrf_dag_kernel(DagArgs g) {
   }
 }
 
+// Resident CTAs per SM of the persistent grid: more CTAs keep SMs busy while
+// some wait on dependencies, fewer give the critical-path tiles a larger share
+// of each SM's FP64 pipe.  BTA_DAG_CTAS_PER_SM overrides the default.
+int dag_ctas_per_sm() {
+  static int v = [] {
+    const char* e = getenv("BTA_DAG_CTAS_PER_SM");
+    int x = e ? atoi(e) : 2;
+    return x < 1 ? 1 : (x > 8 ? 8 : x);
+  }();
+  return v;
+}
+
+// Whether bulk tasks yield the SM to chain tasks (BTA_DAG_YIELD=0 disables).
+int dag_yield() {
+  static int v = [] {
+    const char* e = getenv("BTA_DAG_YIELD");
+    return e ? (atoi(e) != 0) : 1;
+  }();
+  return v;
+}
+
 }  // namespace
 
 int potrf_dag_tasks(int p) {
-  int tot = 0;
-  for (int k = 0; k < p; ++k)
-    tot += 1 + (p - 1 - k) + k + (p - 1 - k) * (p - k) / 2 + (p - 1 - k) * (k + 1);
+  int tot = 1;
+  for (int k = 0; k < p; ++k) tot += step_tasks(p, k);
   return tot;
 }
 
-size_t potrf_dag_state_ints(int p) { return (size_t)4 * p * p + p + 64; }
+size_t potrf_dag_state_ints(int p) { return (size_t)4 * p * p + p + 64 + 256; }
 
 // scratch[z] holds the packed L tiles (p(p-1)/2 tiles) followed by the
 // counters; n*n doubles are enough.
@@ -387,10 +506,10 @@ bta_status potrf_dag_batch(int count, double* const* A, int n, int ld, double* c
     int acc = 0;
     for (int k = 0; k < p; ++k) {
       g.off[k] = acc;
-      acc += 1 + (p - 1 - k) + k + (p - 1 - k) * (p - k) / 2 + (p - 1 - k) * (k + 1);
+      acc += step_tasks(p, k);
     }
     g.off[p] = acc;
-    g.total = acc * cnt;
+    g.total = (acc + 1) * cnt;
     for (int z = 0; z < cnt; ++z) {
       DagInst& I = g.inst[z];
       I.A = A[z0 + z];
@@ -404,7 +523,9 @@ bta_status potrf_dag_batch(int count, double* const* A, int n, int ld, double* c
     // ticket counter and abort flag live after instance 0's counters
     g.counter = g.inst[0].st + 4 * p * p + p + 8;
     g.abort = g.counter + 16;
-    const int grid = std::min(g.total, 152 * 3);
+    g.smbusy = g.inst[0].st + 4 * p * p + p + 64;
+    g.yield = cnt <= 2 ? dag_yield() : 0;
+    const int grid = std::min(g.total, 152 * dag_ctas_per_sm());
     launch_prio(potrf_dag_kernel, dim3(grid), dim3(kDagThreads), s, g);
     BTA_LAUNCHED();
   }
