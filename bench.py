@@ -38,6 +38,18 @@ WORKLOAD = "st_medium"
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
+def reduce_replicas(times, dist=None, device="cpu"):
+    """Replica timing over ranks: each entry becomes its maximum over all ranks
+    (the slowest replica sets the step time).  Without a process group the
+    times are returned unchanged."""
+    if dist is None or dist.get_world_size() == 1:
+        return [float(t) for t in times]
+    import torch
+    tt = torch.tensor([float(t) for t in times], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return [float(v) for v in tt.tolist()]
+
+
 def _flops_model(b, n, a):
     """Algorithmic FP64 flops of one f+grad and of one value-only evaluation
     with the block kernels as implemented (per matrix and block: factor
@@ -299,12 +311,7 @@ def main():
     launches = model.kernel_launches() - k0
     ms = e0.elapsed_time(e1) / args.steps
     t_step = ms * 1e-3
-    if dist is not None:
-        tt = torch.tensor([t_step, float(np.mean(host_times))], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step, t_host = float(tt[0]), float(tt[1])
-    else:
-        t_host = float(np.mean(host_times))
+    t_step, t_host = reduce_replicas([t_step, float(np.mean(host_times))], dist, device="cuda")
     value = world / t_step
     e2e = world / t_host
 
@@ -355,7 +362,7 @@ def main():
     # --- dominant kernel roofline
     gemm_ms, gemm_tf = gemm_roofline(P, torch, prob.b)
 
-    parts = model.last_parts()
+    parts = parts64          # the FP64 evaluation at theta
     flops_grad, flops_val = _flops_model(prob.b, prob.nt, prob.a)
     step_tf = flops_grad / t_step / 1e12
     out = None
