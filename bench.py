@@ -153,11 +153,12 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def gemm_roofline(P, torch, b, reps=5, mixed=False):
-    """Average duration of the FP64 tile GEMM (or, mixed=True, of the
-    split-TF32 tensor-core GEMM with its operand splitting) at the sweep's
-    dense block shape (b x b x b, the Z_B = -Z_D,i+1 F_B product of the
-    selected inversion), timed with CUDA events on its launch stream."""
+def gemm_roofline(P, torch, b, reps=5, mixed=0):
+    """Average duration of the FP64 tile GEMM (mixed=1: the split-TF32
+    tensor-core GEMM with its operand splitting; mixed=2: the FP64 GEMM
+    emulated from 8 BF16 slices, splitting included) at the sweep's dense
+    block shape (b x b x b, the Z_B = -Z_D,i+1 F_B product of the selected
+    inversion), timed with CUDA events on its launch stream."""
     import ctypes as C
     from paper_2605_06392_gb300._capi import lib
     A = torch.randn(b, b, dtype=torch.float64, device="cuda")
@@ -169,6 +170,11 @@ def gemm_roofline(P, torch, b, reps=5, mixed=False):
     def one():
         if not mixed:
             P.bta_gemm(A, B, Cm, stream=s)
+        elif mixed == 2:
+            lib().bta_gemm_emulated(b, b, b, 1.0, C.c_void_p(A.data_ptr()), b, 0,
+                                    C.c_void_p(B.data_ptr()), b, 0, 0.0,
+                                    C.c_void_p(Cm.data_ptr()), b, 8, C.c_void_p(st.data_ptr()),
+                                    C.c_void_p(s.cuda_stream))
         else:
             lib().bta_gemm_mixed(b, b, b, 1.0, C.c_void_p(A.data_ptr()), b, 0,
                                  C.c_void_p(B.data_ptr()), b, 0, 0.0, C.c_void_p(Cm.data_ptr()),
@@ -217,7 +223,7 @@ def run_batch(args, P, torch, workloads):
     print(json.dumps({
         "mode": "batch", "instances": len(probs), "grids": list(grids), "nt": args.batch_nt,
         "b_values": sorted(set(b_list)), "b_counts": {str(v): b_list.count(v) for v in set(b_list)},
-        "precision": "mixed" if prec else "f64", "reps": reps,
+        "precision": {0: "f64", 1: "mixed", 2: "emulated f64"}[prec], "reps": reps,
         "seconds_sequential": t_seq, "seconds_one_graph": t_batch,
         "speedup_one_graph": t_seq / t_batch, "gradients_per_s_one_graph": len(probs) / t_batch,
         "identical_results": same, "algorithmic_tflop": flops / 1e12,
@@ -225,6 +231,24 @@ def run_batch(args, P, torch, workloads):
     batch.close()
     for m in models:
         m.close()
+
+
+def run_step(args, model, theta, torch, stream):
+    """Value-and-gradient steps at one precision (0 FP64, 1 mixed, 2 emulated
+    FP64), the timed ones inside the profiler range (for launch lists)."""
+    for _ in range(args.warmup):
+        model.value_and_grad(theta, precision=args.precision)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.cudart().cudaProfilerStart()
+    e0.record(stream)
+    for _ in range(args.steps):
+        f, g = model.value_and_grad(theta, precision=args.precision)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.cudart().cudaProfilerStop()
+    print(json.dumps({"mode": "step", "precision": args.precision,
+                      "ms_per_step": e0.elapsed_time(e1) / args.steps, "f": f}), flush=True)
 
 
 def main():
@@ -241,10 +265,12 @@ def main():
     ap.add_argument("--instances", type=int, default=31, help="batch mode: number of models")
     ap.add_argument("--grids", default="16,24,32", help="batch mode: grid sides drawn per model")
     ap.add_argument("--batch-nt", type=int, default=40, help="batch mode: time blocks per model")
-    ap.add_argument("--precision", type=int, default=0, help="batch mode: 0 FP64, 1 mixed")
-    ap.add_argument("--mode", default="full", choices=["full", "gemm", "batch"],
+    ap.add_argument("--precision", type=int, default=0,
+                    help="batch / gemm / step modes: 0 FP64, 1 mixed, 2 emulated FP64")
+    ap.add_argument("--mode", default="full", choices=["full", "gemm", "batch", "step"],
                     help="gemm: only the dominant kernel at the sweep's block shape "
-                         "(the small case used for ncu captures)")
+                         "(the small case used for ncu captures); step: only the timed "
+                         "value-and-gradient steps at --precision, inside the profiler range")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -270,8 +296,9 @@ def main():
         return run_batch(args, P, torch, workloads)
     if args.mode == "gemm":
         b = workloads.WORKLOADS[WORKLOAD]["nx"] * workloads.WORKLOADS[WORKLOAD]["ny"]
-        ms, tf = gemm_roofline(P, torch, b, reps=args.steps, mixed=bool(args.precision))
-        name = "tc_gemm_tf32x3_kernel (+ split)" if args.precision else "gemm_f64_kernel"
+        ms, tf = gemm_roofline(P, torch, b, reps=args.steps, mixed=args.precision)
+        name = {0: "gemm_f64_kernel", 1: "tc_gemm_tf32x3_kernel (+ split)",
+                2: "ozaki_gemm_kernel<8> (+ split)"}[args.precision]
         print(json.dumps({"kernel": name, "shape": [b, b, b], "launch_ms": ms,
                           "tflops_fp64_equivalent": tf}), flush=True)
         return
@@ -280,6 +307,8 @@ def main():
     model = P.InlaModel(prob)
     theta = prob.theta.copy()
     stream = torch.cuda.current_stream()
+    if args.mode == "step":
+        return run_step(args, model, theta, torch, stream)
     # warm-up (also captures the CUDA graphs)
     for _ in range(args.warmup):
         f, g = model.value_and_grad(theta)
@@ -336,6 +365,7 @@ def main():
 
     # --- mixed precision (tensor-core split-TF32 Schur products, FP64 diagonal
     # factors / log-dets / refinement): time and error against the FP64 path
+    f, g = model.value_and_grad(theta)              # FP64 at theta (after the FD points)
     x64 = model.mode().cpu().numpy()
     parts64 = model.last_parts()
     for _ in range(2):
@@ -358,6 +388,27 @@ def main():
              "rel_err_grad": [float(v) for v in np.abs(gm - g) / gscale],
              "reference": "FP64 GPU path of this run (itself within 1e-10 of the FP64 oracle)"}
     del pm
+
+    # --- emulated FP64 (the b x b products from 8 BF16 slices on the tensor
+    # cores, everything else FP64): time and difference from the FP64 path
+    emulated = None
+    if prob.b <= 5120:
+        for _ in range(2):
+            fe, ge = model.value_and_grad(theta, precision=2)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            fe, ge = model.value_and_grad(theta, precision=2)
+        e1.record(stream)
+        e1.synchronize()
+        t_emu = e0.elapsed_time(e1) / args.steps * 1e-3
+        xe = model.mode().cpu().numpy()
+        emulated = {"ms_per_step": 1e3 * t_emu, "gradients_per_s": 1.0 / t_emu,
+                    "speedup_vs_fp64": t_step / t_emu,
+                    "rel_err_f": abs(fe - f) / abs(f),
+                    "rel_err_x": float(np.max(np.abs(xe - x64)) / np.max(np.abs(x64))),
+                    "rel_err_grad": [float(v) for v in np.abs(ge - g) / gscale],
+                    "reference": "FP64 GPU path of this run"}
 
     # --- dominant kernel roofline
     gemm_ms, gemm_tf = gemm_roofline(P, torch, prob.b)
@@ -391,6 +442,7 @@ def main():
                             "max_rel_diff_fd_vs_ad": float(np.max(np.abs(g_fd - g) /
                                                                   np.maximum(np.abs(g), 1.0)))},
             "mixed_precision": mixed,
+            "emulated_fp64": emulated,
             "fp64_step": {"algorithmic_tflop_per_step": flops_grad / 1e12,
                           "achieved_tflops": step_tf, "frac_of_peak": step_tf / FP64_PEAK_TFLOPS},
             "roofline": {"bound": "alu", "kernel": "gemm_f64_kernel<32,32> at b x b x b",

@@ -107,7 +107,11 @@ typedef struct {
                           and the selected-inversion products in split TF32
                           on the tensor cores (FP32 accumulation); diagonal
                           block factorisation, log-determinants, arrow and tip
-                          in FP64; one FP64 refinement step on x*            */
+                          in FP64; one FP64 refinement step on x*.
+                          2: emulated FP64 -- the same b x b products as in
+                          mode 1 computed to FP64 accuracy on the BF16 tensor
+                          cores (8 slices, as bta_gemm_emulated; b <= 5120),
+                          everything else as in mode 0                        */
   int32_t use_graph;   /* 1: capture the evaluation in a CUDA graph, replay */
   int32_t streams;     /* thetas evaluated together for batch > 1 (1..16): their
                           matrices are swept in the same batched launches;
@@ -280,6 +284,25 @@ bta_status bta_gemm_mixed(int32_t M, int32_t N, int32_t K, double alpha, const d
                           int32_t lda, int32_t transA, const double* B, int32_t ldb,
                           int32_t transB, double beta, double* C, int32_t ldc, int32_t* status,
                           cudaStream_t stream);
+
+/*
+ * bta_gemm_emulated -- the same product as bta_gemm to FP64 accuracy on the
+ * BF16 tensor cores (the products of the emulated-FP64 mode, the Ozaki
+ * error-free splitting; no counterpart in the paper, whose GPUs have FP64
+ * tensor cores): each row of op(A) and column of op(B) is scaled by a power
+ * of two and written as `slices` (6..8) signed base-128 digits (7 bits
+ * each: 8 slices carry 56 bits, more than FP64's 53), the slice products
+ * of the leading levels accumulate exactly in FP32 and are summed in 64-bit
+ * integers, and the result is rounded once to FP64.  Error per entry at most
+ * (slices + 4) 2^(-7 slices) K max_k|a_ik| max_k|b_kn| plus the final
+ * rounding (slices = 8: the order of an FP64 GEMM's rounding bound).  Requires 1 <= K <= 5120.  status as for
+ * bta_gemm_mixed.  Allocates its operand slices with cudaMallocAsync on
+ * the stream.
+ */
+bta_status bta_gemm_emulated(int32_t M, int32_t N, int32_t K, double alpha, const double* A,
+                             int32_t lda, int32_t transA, const double* B, int32_t ldb,
+                             int32_t transB, double beta, double* C, int32_t ldc,
+                             int32_t slices, int32_t* status, cudaStream_t stream);
 
 /*
  * inla_grid_stencil -- spatial base matrices of an nx x ny grid model

@@ -84,6 +84,10 @@ SIGNATURES = {
     "bta_gemm_mixed": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_void_p,
                                  C.c_int32, C.c_int32, C.c_void_p, C.c_int32, C.c_int32,
                                  C.c_double, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
+    "bta_gemm_emulated": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_void_p,
+                                    C.c_int32, C.c_int32, C.c_void_p, C.c_int32, C.c_int32,
+                                    C.c_double, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
+                                    C.c_void_p]),
     "inla_grid_stencil": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(C.c_int32), C.c_void_p,
                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
 }

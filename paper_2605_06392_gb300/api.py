@@ -256,6 +256,24 @@ def bta_gemm(A: torch.Tensor, B: torch.Tensor, C_out: torch.Tensor, alpha: float
           "bta_gemm")
 
 
+def bta_gemm_emulated(A: torch.Tensor, B: torch.Tensor, C_out: torch.Tensor, alpha: float = 1.0,
+                      beta: float = 0.0, transA: bool = False, transB: bool = False,
+                      slices: int = 8, stream=None) -> torch.Tensor:
+    """As bta_gemm, computed to FP64 accuracy on the BF16 tensor cores from
+    `slices` base-128 digits per operand (bta_gemm_emulated).  Returns the
+    device status word (0, or BTA_ERR_TIMEOUT if a bounded wait expired)."""
+    M = A.shape[0] if transA else A.shape[1]
+    K = A.shape[1] if transA else A.shape[0]
+    N = B.shape[1] if transB else B.shape[0]
+    st = torch.zeros(1, dtype=torch.int32, device=C_out.device)
+    check(lib().bta_gemm_emulated(M, N, K, alpha, C.c_void_p(A.data_ptr()), A.shape[1],
+                                  int(transA), C.c_void_p(B.data_ptr()), B.shape[1], int(transB),
+                                  beta, C.c_void_p(C_out.data_ptr()), C_out.shape[1], slices,
+                                  C.c_void_p(st.data_ptr()), _stream(stream)),
+          "bta_gemm_emulated")
+    return st
+
+
 class InlaBatch:
     """Several models evaluated by one CUDA graph launch
     (inla_batch_value_and_grad): each model's whole evaluation is a branch of

@@ -69,8 +69,8 @@ struct inla_model {
 // Several models evaluated by one CUDA graph (see inla_batch_value_and_grad).
 struct inla_batch {
   std::vector<inla_model*> models;
-  cudaGraphExec_t exec[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};   // [grad][precision]
-  int64_t kernels[2][2] = {{0, 0}, {0, 0}};
+  cudaGraphExec_t exec[2][3] = {};   // [grad][precision]
+  int64_t kernels[2][3] = {};
   cudaEvent_t fork = nullptr;
 };
 
@@ -138,8 +138,9 @@ bta_status ctx_alloc(inla_model* m, EvalCtx& c) {
   BTA_TRY(dmalloc(m, &wsbuf, 2 * wsb));
   c.wsc.carve(wsbuf, ld, a);
   c.wsp.carve(wsbuf + wsb, ld, a);
-  // mixed precision: operand copies of the tensor-core products, one per sweep
-  const size_t tcb = tc_gemm_ws_bytes(ld, ld, ld);
+  // tensor-core modes: operand copies of the tensor-core products, one per sweep
+  const size_t tcb = std::max(tc_gemm_ws_bytes(ld, ld, ld),
+                              ld <= 5120 ? ozaki_ws_bytes(ld, ld, ld, 8) : (size_t)0);
   uint8_t* tcbuf = nullptr;
   BTA_TRY(dmalloc(m, &tcbuf, 2 * tcb));
   c.wsc.tc = tcbuf;
@@ -203,7 +204,7 @@ bta_status record_group(inla_model* m, int mode, int cnt, int prec, cudaStream_t
       BTA_TRY(launch_assemble(md, m->L, m->ctx[e].coefbuf, 1, m->ctx[e].qc, m->ctx[e].x, m->s1));
     BTA_TRY(factor_sweep_multi(ic.data(), cnt, m->s1, m->evd, prec));
     BTA_TRY(upper_solve_multi(ic.data(), cnt, m->s1));
-    if (prec) {
+    if (prec == 1) {
       // one step of iterative refinement in FP64: x += Q_c^{-1} (r - Q_c x)
       for (int e = 0; e < cnt; ++e) {
         EvalCtx& c = m->ctx[e];
@@ -600,7 +601,7 @@ bta_status inla_value_and_grad(inla_model* m, const double* theta, int32_t batch
                                double* grad, const inla_opts* opts, cudaStream_t stream) {
   if (!m || !theta || !f || batch < 1) return BTA_ERR_ARG;
   const int prec = opts ? opts->precision : 0;
-  if (prec != 0 && prec != 1) return BTA_ERR_ARG;
+  if (prec < 0 || prec > 2) return BTA_ERR_ARG;
   for (int i = 0; i < batch; ++i)
     if (!finite_theta(theta + (size_t)i * m->d, m->d)) return BTA_ERR_ARG;
   const int use_graph = opts ? opts->use_graph : 1;
@@ -664,6 +665,24 @@ bta_status bta_gemm_mixed(int32_t M, int32_t N, int32_t K, double alpha, const d
   return st;
 }
 
+bta_status bta_gemm_emulated(int32_t M, int32_t N, int32_t K, double alpha, const double* A,
+                             int32_t lda, int32_t transA, const double* B, int32_t ldb,
+                             int32_t transB, double beta, double* Cm, int32_t ldc,
+                             int32_t slices, int32_t* status, cudaStream_t stream) {
+  if (M < 0 || N < 0 || K < 1 || K > 5120 || !A || !B || !Cm || slices < 6 || slices > 8)
+    return BTA_ERR_ARG;
+  Gemm g;
+  g.M = M; g.N = N; g.K = K; g.alpha = alpha; g.beta = beta;
+  g.A = A; g.lda = lda; g.transA = transA ? 1 : 0;
+  g.B = B; g.ldb = ldb; g.transB = transB ? 1 : 0;
+  g.C = Cm; g.ldc = ldc; g.Cin = Cm; g.ldcin = ldc;
+  void* ws = nullptr;
+  BTA_CUDA_TRY(cudaMallocAsync(&ws, ozaki_ws_bytes(M, N, K, slices), stream));
+  bta_status st = ozaki_gemm(g, ws, status, slices, stream);
+  cudaFreeAsync(ws, stream);
+  return st;
+}
+
 bta_status inla_batch_create(inla_model* const* models, int32_t count, inla_batch** out) {
   if (!models || !out || count < 1) return BTA_ERR_ARG;
   *out = nullptr;
@@ -714,7 +733,7 @@ bta_status inla_batch_value_and_grad(inla_batch* b, const double* theta, int32_t
                                      double* grad, const inla_opts* opts, cudaStream_t stream) {
   if (!b || !theta || !f || ldt < 1) return BTA_ERR_ARG;
   const int prec = opts ? opts->precision : 0;
-  if (prec != 0 && prec != 1) return BTA_ERR_ARG;
+  if (prec < 0 || prec > 2) return BTA_ERR_ARG;
   const int g = grad ? 1 : 0;
   const int nm = (int)b->models.size();
   for (int i = 0; i < nm; ++i) {

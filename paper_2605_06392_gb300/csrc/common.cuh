@@ -137,6 +137,11 @@ constexpr int kGemvSplit = 16;      // K splits; work needs kGemvSplit * M doubl
 // inside the kernel expired.
 bta_status tc_gemm_mixed(const Gemm& g, void* ws, int32_t* status, cudaStream_t s);
 size_t tc_gemm_ws_bytes(int M, int N, int K);
+// FP64 GEMM emulated on BF16 tensor cores with `slices` (6..8) base-128
+// digits per operand (ozaki_gemm.cu); single problem, K <= 5120.
+bta_status ozaki_gemm(const Gemm& g, void* ws, int32_t* status, int slices, cudaStream_t s);
+size_t ozaki_ws_bytes(int M, int N, int K, int slices);
+bool ozaki_supported(const Gemm& g);
 
 // ----------------------------------------------------------------------------
 // Diagonal-block Cholesky + inverse (potrf.cu)

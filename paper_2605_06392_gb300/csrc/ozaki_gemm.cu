@@ -1,0 +1,651 @@
+// FP64 GEMM emulated on BF16 tensor cores by error-free operand splitting
+// (Ozaki, Ogita, Oishi and Rump, "Error-free transformations of matrix
+// multiplication by using fast routines of matrix multiplication and its
+// applications", Numer. Algorithms 59, 2012; the fixed-point slice form
+// follows Mukunoki, Ozaki, Ogita and Imamura, "DGEMM using Tensor Cores,
+// and its accurate and reproducible versions", ISC 2020):
+//
+//   C = alpha op(A) op(B) + beta C,   FP64 in and out.
+//
+// Splitting.  Row i of op(A) is scaled by a power of two 2^(e_i) with
+// |a_ik| < 2^(e_i + 7) and written in S signed base-128 digits:
+//     a_ik = 2^(e_i) * sum_j d_j(a_ik) * 2^(-7(j-1)),   |d_1| <= 128, |d_j| <= 64,
+// each digit rounded to nearest from the fixed-point value of a_ik with
+// 7S fractional bits (S = 8: 56 bits, one more than the 53 of an FP64
+// significand).  Column n of op(B) likewise with 2^(f_n).  Every digit
+// times its power of two is exact in BF16 (<= 8 significant bits), so each
+// slice A_j, B_l is a BF16 matrix and each slice product A_j B_l is exact
+// in its terms.
+//
+// Products.  C = 2^(e_i + f_n) sum over pairs (j, l) with j + l <= S + 1 of
+// A_j B_l (the pairs beyond are below the 7S-bit truncation).  The pairs
+// of one level L = j + l share the scale 2^(-7(L-2)), so their sum over
+// k is an integer multiple of it; with the digit bounds above it stays
+// within 2^24 units over 512 consecutive k for L <= 7, so an FP32
+// accumulator holds it exactly.  Levels 2..7 therefore run on tcgen05
+// (kind::f16, BF16 operands, FP32 accumulator in tensor memory) into one
+// accumulator per level, drained into 64-bit integers every 512 of K;
+// levels 8..S+1 (relative weight <= 2^-42) share one FP32 accumulator over
+// the whole K, whose rounding (2^-24 of it) stays far below the FP64 unit.
+// The FP64 result is assembled from the integer sum and that accumulator
+// with integer operations (GB300's FP64 pipe runs more than 1000x slower than
+// its BF16 tensor cores, so the epilogue avoids it except for the beta C add).
+//
+// Kernel: one 128 x 64 output tile per CTA (1 CTA per SM), 192 threads.
+//   * warp 4 streams 32-wide K slabs of the S A-slices and S B-slices into a
+//     2-stage shared-memory ring with TMA (64-byte swizzle);
+//   * warp 5 issues the S(S+1)/2 slice-pair MMAs (M=128, N=64, K=16) per 16
+//     of K into the seven TMEM accumulators (7 x 64 columns), from lane 0
+//     of the converged warp;
+//   * warps 0-3 drain the exact accumulators (one TMEM lane quarter each)
+//     every 512 of K and write the tile.
+// Every mbarrier wait is bounded: on expiry the kernel records
+// BTA_ERR_TIMEOUT in the status word, stops issuing work, waits (bounded)
+// for the loads and MMAs it issued and frees its tensor memory.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "tma.cuh"
+
+namespace bta {
+namespace {
+
+using namespace tc;
+
+constexpr int OM = 128;                 // tile rows = TMEM lanes
+constexpr int OBN = 64;                 // tile columns
+constexpr int OK16 = 32;                // bf16 per K slab: 64-byte rows
+constexpr int kOzStages = 2;
+constexpr int kChunkSlabs = 16;         // exact accumulators drained every 512 of K
+constexpr int kOzThreads = 192;   // warps 0-3 drain, 4 loads, 5 issues MMAs
+constexpr int kMaxOzK = 5120;           // keeps the 64-bit integer sum below 2^62.4
+constexpr long long kOzWaitLimit = 1ll << 21;
+constexpr int kATile = OM * OK16 * 2;   // 8 KB
+constexpr int kBTile = OBN * OK16 * 2;  // 4 KB
+
+template <int S>
+struct OzCfg {
+  static_assert(S >= 6 && S <= 8, "levels 2..7 exact, 8..S+1 in one rounded accumulator");
+  static constexpr bool kRounded = S >= 7;   // some pair has level >= 8
+  static constexpr int kStage = S * (kATile + kBTile);
+  static constexpr int kSmem = kOzStages * kStage + 1024 + 512;
+  static constexpr uint32_t kTmemCols = 512;
+  // kind::f16: FP32 accumulator, A and B BF16, both K-major, N = 64, M = 128
+  static constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                                     ((uint32_t)(OBN >> 3) << 17) | ((uint32_t)(OM >> 4) << 24);
+};
+
+// Shared-memory matrix descriptor: K-major operand, 64-byte swizzle, 8-row
+// groups 512 bytes apart.
+__device__ __forceinline__ uint64_t sdesc64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);   // start address
+  d |= (uint64_t)1 << 16;                     // leading-dimension offset (unused)
+  d |= (uint64_t)(512 >> 4) << 32;            // stride between 8-row groups
+  d |= (uint64_t)1 << 46;                     // descriptor version
+  d |= (uint64_t)4 << 61;                     // 64-byte swizzle
+  return d;
+}
+
+// The MMA of slice pair (J, LL) (0-based digits of A and B, level
+// L = J + LL + 2) for the 16-wide K step KK of the stage whose descriptor
+// base is dst; issued by one lane (leader != 0) of a converged warp.  The
+// operand offsets are immediates, so no descriptor lives in a register.
+// The first MMA of a level in a slab overwrites its accumulator when the
+// slab opens a 512-wide K chunk (exact levels) or the whole K range (the
+// rounded accumulator of levels >= 8).
+template <int S, int J, int LL, int KK>
+__device__ __forceinline__ void issue_pair(uint32_t tmem, uint64_t dst, uint32_t chunk_first,
+                                           uint32_t kernel_first, uint32_t leader) {
+  constexpr int L = J + LL + 2;
+  constexpr int kAccIdx = L <= 7 ? L - 2 : 6;
+  constexpr bool kFirstInSlab = KK == 0 && J == 0 && L <= 8;
+  const uint32_t accumulate =
+      kFirstInSlab ? ((L <= 7 ? chunk_first : kernel_first) ? 0u : 1u) : 1u;
+  constexpr unsigned long long kAo = (unsigned long long)(J * kATile + KK * 32) >> 4;
+  constexpr unsigned long long kBo =
+      (unsigned long long)(S * kATile + LL * kBTile + KK * 32) >> 4;
+  asm volatile(
+      "{\n .reg .b64 da, db;\n .reg .pred p, e;\n"
+      " add.s64 da, %1, %2;\n add.s64 db, %1, %3;\n"
+      " setp.ne.b32 p, %5, 0;\n setp.ne.b32 e, %6, 0;\n"
+      " @e tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %4, p;\n}\n" ::"r"(
+          tmem + (uint32_t)(kAccIdx * OBN)),
+      "l"(dst), "n"(kAo), "n"(kBo), "r"(OzCfg<S>::kIdesc), "r"(accumulate), "r"(leader)
+      : "memory");
+}
+
+template <int S, int J, int LL, int KK>
+__device__ __forceinline__ void issue_row(uint32_t tmem, uint64_t dst, uint32_t cf, uint32_t kf,
+                                          uint32_t leader) {
+  if constexpr (J + LL < S) {
+    issue_pair<S, J, LL, KK>(tmem, dst, cf, kf, leader);
+    issue_row<S, J, LL + 1, KK>(tmem, dst, cf, kf, leader);
+  }
+}
+
+template <int S, int J, int KK>
+__device__ __forceinline__ void issue_step(uint32_t tmem, uint64_t dst, uint32_t cf, uint32_t kf,
+                                           uint32_t leader) {
+  if constexpr (J < S) {
+    issue_row<S, J, 0, KK>(tmem, dst, cf, kf, leader);
+    issue_step<S, J + 1, KK>(tmem, dst, cf, kf, leader);
+  }
+}
+
+__device__ __forceinline__ void mma_commit_if(uint32_t mbar, uint32_t leader) {
+  asm volatile(
+      "{\n .reg .pred e;\n setp.ne.b32 e, %1, 0;\n"
+      " @e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n" ::"r"(
+          mbar),
+      "r"(leader)
+      : "memory");
+}
+
+// Bounded wait by lane 0, result broadcast: a warp-uniform decision.
+__device__ __forceinline__ bool warp_wait(uint32_t addr, uint32_t parity, int lane) {
+  int ok = 0;
+  if (lane == 0) ok = mbar_wait(addr, parity, kOzWaitLimit) ? 1 : 0;
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+// A shared flag read by lane 0 and broadcast.
+__device__ __forceinline__ bool warp_flag(const int* f, int lane) {
+  int v = 0;
+  if (lane == 0) v = *(const volatile int*)f;
+  return __shfl_sync(0xffffffffu, v, 0) != 0;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t addr) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(addr) : "memory");
+}
+
+// OR of v over the 128 threads of warps 0-3 (named barrier 1).
+__device__ __forceinline__ int bar_or_128(int v) {
+  int r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.s32 p, %1, 0;\n"
+      " barrier.cta.red.or.pred q, 1, 128, p;\n selp.s32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"(v)
+      : "memory");
+  return r;
+}
+
+// X * 2^E rounded to the nearest double, from the integer X by integer
+// operations (the usual case); out-of-range exponents take ldexp.
+__device__ __forceinline__ double compose(long long X, int E) {
+  if (X == 0) return 0.0;
+  const unsigned long long sgn = X < 0 ? (1ull << 63) : 0ull;
+  unsigned long long u = X < 0 ? 0ull - (unsigned long long)X : (unsigned long long)X;
+  int lz = __clzll((long long)u);
+  u <<= lz;                                   // leading one at bit 63
+  unsigned long long m = u >> 11;             // 53 significant bits
+  const unsigned long long rem = u & 0x7FFull;
+  if (rem > 0x400ull || (rem == 0x400ull && (m & 1ull))) {
+    ++m;
+    if (m >> 53) { m >>= 1; --lz; }
+  }
+  const int be = 1023 + (63 - lz) + E;
+  if (be <= 0 || be >= 2047) return ldexp((double)X, E);
+  return __longlong_as_double((long long)(sgn | ((unsigned long long)be << 52) |
+                                          (m & ((1ull << 52) - 1))));
+}
+
+struct OzArgs {
+  int M, N, Kp, Mp, Np;
+  double alpha, beta;
+  double* C;
+  int ldc;
+  const double* Cin;
+  int ldcin;
+  int out_lower;
+  const int* exA;   // [Mp] biased exponent bound of each row of op(A)
+  const int* exB;   // [Np] biased exponent bound of each column of op(B)
+  long long* partial;   // [Np][Mp] integer sums between K chunks (K > 512 only)
+  int32_t* status;
+};
+
+template <int S>
+__global__ void __launch_bounds__(kOzThreads, 1)
+    ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA,
+                      const __grid_constant__ CUtensorMap mB, OzArgs g) {
+  using Cfg = OzCfg<S>;
+  const int m0 = blockIdx.x * OM, n0 = blockIdx.y * OBN;
+  if (g.out_lower && n0 > m0 + OM - 1) return;   // whole CTA exits before any set-up
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kOzStages * Cfg::kStage);
+  // bars: full[stages], empty[stages], accumulators full, accumulators drained, final
+  const int kFull = 0, kEmpty = kOzStages, kAccFull = 2 * kOzStages,
+            kAccEmpty = 2 * kOzStages + 1, kFinal = 2 * kOzStages + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kOzStages + 3);
+  int* s_exB = reinterpret_cast<int*>(tmem_slot + 4);   // [OBN]
+  __shared__ int s_abort, s_issued, s_consumed;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nk = g.Kp / OK16;
+  const int nchunks = (nk + kChunkSlabs - 1) / kChunkSlabs;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kOzStages; ++s) {
+      mbar_init(smem_u32(&bars[kFull + s]), 1);
+      mbar_init(smem_u32(&bars[kEmpty + s]), 1);
+    }
+    mbar_init(smem_u32(&bars[kAccFull]), 1);
+    mbar_init(smem_u32(&bars[kAccEmpty]), 128);
+    mbar_init(smem_u32(&bars[kFinal]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_abort = 0;
+    s_issued = 0;
+    s_consumed = 0;
+  }
+  for (int i = threadIdx.x; i < OBN; i += kOzThreads) s_exB[i] = g.exB[n0 + i];
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(Cfg::kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 4) {
+    // ---- TMA producer: slab kt of every slice into stage kt % stages
+    const uint32_t leader = lane == 0;
+    for (int kt = 0; kt < nk; ++kt) {
+      const int s = kt % kOzStages;
+      if (kt >= kOzStages &&
+          !warp_wait(smem_u32(&bars[kEmpty + s]), (uint32_t)((kt / kOzStages - 1) & 1), lane)) {
+        if (leader) atomicExch(&s_abort, 1);
+        break;
+      }
+      if (warp_flag(&s_abort, lane)) break;
+      if (leader) {
+        const uint32_t full = smem_u32(&bars[kFull + s]);
+        mbar_expect_tx(full, Cfg::kStage);
+        uint8_t* st = smem + s * Cfg::kStage;
+        const int k0 = kt * OK16;
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+          tma_load_2d(smem_u32(st + j * kATile), &mA, full, k0, j * g.Mp + m0);
+          tma_load_2d(smem_u32(st + S * kATile + j * kBTile), &mB, full, k0, j * g.Np + n0);
+        }
+        *(volatile int*)&s_issued = kt + 1;
+      }
+      __syncwarp();
+    }
+  } else if (warp == 5) {
+    // ---- MMA issuer: the whole warp runs the loop, lane 0 issues
+    const uint32_t leader = lane == 0;
+    const uint64_t dbase = sdesc64(smem_u32(smem));   // + (byte offset >> 4) per operand tile
+    bool stop = false;
+    for (int c = 0; c < nchunks && !stop; ++c) {
+      if (c > 0 && !warp_wait(smem_u32(&bars[kAccEmpty]), (uint32_t)((c - 1) & 1), lane)) {
+        stop = true;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int kt1 = min(nk, (c + 1) * kChunkSlabs);
+      for (int kt = c * kChunkSlabs; kt < kt1; ++kt) {
+        const int s = kt % kOzStages;
+        if (warp_flag(&s_abort, lane) ||
+            !warp_wait(smem_u32(&bars[kFull + s]), (uint32_t)((kt / kOzStages) & 1), lane)) {
+          stop = true;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint64_t dst = dbase + (uint64_t)((s * Cfg::kStage) >> 4);
+        const uint32_t cf = kt == c * kChunkSlabs, kf = kt == 0;
+        issue_step<S, 0, 0>(tmem, dst, cf, kf, leader);   // 16 bf16 = 32 bytes along K
+        issue_step<S, 0, 1>(tmem, dst, cf, kf, leader);
+        mma_commit_if(smem_u32(&bars[kEmpty + s]), leader);   // slab free once these finish
+        if (leader) *(volatile int*)&s_consumed = kt + 1;
+        __syncwarp();
+      }
+      mma_commit_if(smem_u32(&bars[kAccFull]), leader);        // this chunk's sums ready
+    }
+    if (stop) {
+      if (leader) atomicExch(&s_abort, 1);
+      // wait (bounded) for the MMAs this warp issued before leaving
+      mma_commit_if(smem_u32(&bars[kFinal]), leader);
+      warp_wait(smem_u32(&bars[kFinal]), 0, lane);
+    }
+  } else {
+    // ---- warps 0-3: drain the exact accumulators every 512 of K into 64-bit
+    // integer sums (kept in a workspace between chunks), and after the last
+    // chunk assemble and store the tile.  Thread = output row, 32 columns at
+    // a time.
+    const uint32_t lane_off = (uint32_t)(warp * 32) << 16;
+    const int m = m0 + warp * 32 + lane;
+    const int ea = g.exA[m];   // exA has Mp entries
+    int failed = 0;
+    for (int c = 0; c < nchunks; ++c) {
+      const bool ok = mbar_wait(smem_u32(&bars[kAccFull]), (uint32_t)(c & 1), kOzWaitLimit);
+      if (bar_or_128(!ok || *(volatile int*)&s_abort)) {
+        failed = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const bool last = c == nchunks - 1;
+#pragma unroll 1
+      for (int cc = 0; cc < OBN / 32; ++cc) {
+        long long* part = g.partial + m + (int64_t)(n0 + cc * 32) * g.Mp;
+        long long acc[32];
+#pragma unroll
+        for (int q = 0; q < 32; ++q) acc[q] = c > 0 ? part[(int64_t)q * g.Mp] : 0ll;
+        // levels 2..7 in units of level 7 (2^-35)
+#pragma unroll
+        for (int a = 0; a < 6; ++a) {
+          const float up = __int_as_float((127 + 7 * a) << 23);   // level a+2 in integer units
+          const long long sc = 1ll << (7 * (5 - a));
+          float v[32];
+          tmem_ld32(tmem + lane_off + (uint32_t)(a * OBN + cc * 32), v);
+#pragma unroll
+          for (int q = 0; q < 32; ++q) acc[q] += (long long)__float2int_rn(v[q] * up) * sc;
+        }
+        if (!last) {
+#pragma unroll
+          for (int q = 0; q < 32; ++q) part[(int64_t)q * g.Mp] = acc[q];
+          continue;
+        }
+        // the rounded accumulator, assemble, alpha / beta, store
+        float v[32];
+        if (Cfg::kRounded) {
+          tmem_ld32(tmem + lane_off + (uint32_t)(6 * OBN + cc * 32), v);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 32; ++q) v[q] = 0.f;
+        }
+        if (m < g.M) {
+#pragma unroll
+          for (int q = 0; q < 32; ++q) {
+            const int n = n0 + cc * 32 + q;
+            if (n >= g.N || (g.out_lower && m < n)) continue;
+            // sum = (acc + v 2^35) 2^-35
+            const long long X = acc[q] + __float2ll_rn(v[q] * 34359738368.0f);
+            // a = 2^(exA - 1029) sum_j A_j, b likewise: C = X 2^(exA + exB - 2058 - 35)
+            double out = compose(X, ea + s_exB[cc * 32 + q] - 2093);
+            if (g.alpha == -1.0) out = -out;
+            else if (g.alpha != 1.0) out *= g.alpha;
+            if (g.beta == 1.0) out += g.Cin[m + (int64_t)n * g.ldcin];
+            else if (g.beta != 0.0) out = fma(g.beta, g.Cin[m + (int64_t)n * g.ldcin], out);
+            g.C[m + (int64_t)n * g.ldc] = out;
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(smem_u32(&bars[kAccEmpty]));
+    }
+    if (failed && threadIdx.x == 0) atomicExch(&s_abort, 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x == 0 && s_abort) {
+    // loads issued but never consumed: wait (bounded) for them to land
+    for (int kt = s_consumed; kt < s_issued; ++kt)
+      mbar_wait(smem_u32(&bars[kFull + kt % kOzStages]), (uint32_t)((kt / kOzStages) & 1),
+                kOzWaitLimit);
+    if (g.status) atomicExch(g.status, (int)BTA_ERR_TIMEOUT);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(Cfg::kTmemCols)
+                 : "memory");
+  }
+}
+
+// ---- splitting ---------------------------------------------------------------
+
+// Element (r, k) of op(X) masked to its triangle (0 outside).
+__device__ __forceinline__ double op_elem(const double* X, int ldx, int trans, int tri, int r,
+                                          int k) {
+  if ((tri == TRI_LOWER && k > r) || (tri == TRI_UPPER && k < r)) return 0.0;
+  return trans ? X[k + (int64_t)r * ldx] : X[r + (int64_t)k * ldx];
+}
+
+// One operand to split: rows of op(X) (op(B)^T for the B side), their
+// exponent bounds ex[rowsP] and slices Y[S][rowsP][Kp].
+struct SplitOp {
+  const double* X;
+  int ldx, trans, tri, rows, rowsP;
+  int* ex;
+  __nv_bfloat16* Y;
+};
+struct SplitArgs {
+  SplitOp op[2];   // blockIdx.z selects the operand
+  int K, Kp;
+};
+
+// ex[r] = max over k of the biased exponent field of op(X)[r][k] (ex zeroed
+// beforehand).  Block 256 threads over 32 rows x 64 columns of op(X), read
+// in the memory order of X, 8 independent loads per thread.
+__global__ void ozaki_exp_kernel(SplitArgs a) {
+  const SplitOp o = blockIdx.z == 0 ? a.op[0] : a.op[1];
+  const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 64;
+  if (r0 >= o.rows) return;
+  __shared__ int smax[32];
+  const int t = threadIdx.x;
+  if (t < 32) smax[t] = 0;
+  __syncthreads();
+  int e = 0;
+  if (!o.trans) {
+    const int rr = t & 31, r = r0 + rr;   // consecutive threads: consecutive rows
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int k = k0 + (t >> 5) + 8 * i;
+      if (r < o.rows && k < a.K) {
+        const double v = op_elem(o.X, o.ldx, 0, o.tri, r, k);
+        e = max(e, (int)((__double_as_longlong(v) >> 52) & 0x7FF));
+      }
+    }
+    atomicMax(&smax[rr], e);
+  } else {
+    const int kk = t & 63, k = k0 + kk;   // consecutive threads: consecutive k
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int rr = (t >> 6) + 4 * i, r = r0 + rr;
+      int ei = 0;
+      if (r < o.rows && k < a.K) {
+        const double v = op_elem(o.X, o.ldx, 1, o.tri, r, k);
+        ei = (int)((__double_as_longlong(v) >> 52) & 0x7FF);
+      }
+      ei = (int)__reduce_max_sync(0xffffffffu, (unsigned)ei);   // a warp shares rr
+      if ((t & 31) == 0) atomicMax(&smax[rr], ei);
+    }
+  }
+  __syncthreads();
+  if (t < 32 && r0 + t < o.rows && smax[t] > 0) atomicMax(&o.ex[r0 + t], smax[t]);
+}
+
+// The S signed base-128 digits of v for the row exponent bound er, each
+// times its power of two (exact in BF16).
+template <int S>
+__device__ __forceinline__ void digits(double v, int er, float (&out)[S]) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+  const int E = (int)((bits >> 52) & 0x7FF);
+  long long F = 0;   // v 2^(1078 - er): |F| < 2^56
+  if (E != 0) {
+    const unsigned long long mant = (bits & ((1ull << 52) - 1)) | (1ull << 52);
+    const int sh = E - er + 3;   // <= 3
+    if (sh >= 0) {
+      F = (long long)(mant << sh);
+    } else if (sh > -54) {
+      F = (long long)((mant + (1ull << (-sh - 1))) >> (-sh));
+    }
+    if (bits >> 63) F = -F;
+  }
+#pragma unroll
+  for (int j = 0; j < S; ++j) {
+    const int shj = 49 - 7 * j;   // digit j covers bits [shj, shj + 7) of F
+    long long d;
+    if (shj > 0) {
+      // nearest: d = floor((F + h) / 2^shj), remainder (F + h) mod 2^shj - h
+      const long long h = 1ll << (shj - 1);
+      const long long t = F + h;
+      d = t >> shj;
+      F = (t & ((1ll << shj) - 1)) - h;
+    } else {
+      d = F;
+    }
+    out[j] = (float)d * __int_as_float((127 - 7 * j) << 23);
+  }
+}
+
+// Y[j][r][k] (j < S, r < rowsP, k < Kp; K contiguous) = digit j of
+// op(X)[r][k] times 2^(-7j); zero in the padding.  Block 256 threads over
+// 32 rows x 64 columns; each thread writes pairs of columns.
+template <int S>
+__global__ void ozaki_split_kernel(SplitArgs a) {
+  const SplitOp o = blockIdx.z == 0 ? a.op[0] : a.op[1];
+  const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 64;
+  if (r0 >= o.rowsP) return;
+  __shared__ double tile[32][65];   // tile[r - r0][k - k0]
+  const int t = threadIdx.x;
+  if (!o.trans) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int idx = t + 256 * i, rr = idx & 31, kk = idx >> 5;
+      const int r = r0 + rr, k = k0 + kk;
+      tile[rr][kk] = (r < o.rows && k < a.K) ? op_elem(o.X, o.ldx, 0, o.tri, r, k) : 0.0;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int idx = t + 256 * i, kk = idx & 63, rr = idx >> 6;
+      const int r = r0 + rr, k = k0 + kk;
+      tile[rr][kk] = (r < o.rows && k < a.K) ? op_elem(o.X, o.ldx, 1, o.tri, r, k) : 0.0;
+    }
+  }
+  __syncthreads();
+  const size_t plane = (size_t)o.rowsP * a.Kp;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int idx = t + 256 * i, rr = idx >> 5, kp = idx & 31;   // a warp: one row, 64 k
+    const int r = r0 + rr, k = k0 + 2 * kp;
+    if (k >= a.Kp) continue;   // Kp is a multiple of 32 and k even: k + 1 < Kp too
+    const int er = r < o.rows ? o.ex[r] : 0;
+    float d0[S], d1[S];
+    digits<S>(tile[rr][2 * kp], er, d0);
+    digits<S>(tile[rr][2 * kp + 1], er, d1);
+    __nv_bfloat162* y = reinterpret_cast<__nv_bfloat162*>(o.Y + (size_t)r * a.Kp + k);
+#pragma unroll
+    for (int j = 0; j < S; ++j) y[j * plane / 2] = __floats2bfloat162_rn(d0[j], d1[j]);
+  }
+}
+
+// 2D map over Y viewed as (S * rowsP) x Kp BF16, box 32 (K) x boxRows.
+bta_status make_map_bf16(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap* map,
+                         const __nv_bfloat16* base, int rowsAll, int Kp, int boxRows) {
+  cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rowsAll};
+  cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
+  cuuint32_t box[2] = {(cuuint32_t)OK16, (cuuint32_t)boxRows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(base),
+                   dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? BTA_OK : BTA_ERR_ARG;
+}
+
+struct OzLayout {
+  int Mp, Np, Kp;
+  size_t a_off, b_off, ea_off, eb_off, p_off, total;
+  OzLayout(int M, int N, int K, int S) {
+    Mp = cdiv(M, OM) * OM;
+    Np = cdiv(N, OBN) * OBN;
+    Kp = cdiv(K, OK16) * OK16;
+    auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+    a_off = 0;
+    b_off = up((size_t)S * Mp * Kp * 2);
+    ea_off = b_off + up((size_t)S * Np * Kp * 2);
+    eb_off = ea_off + up((size_t)Mp * 4);
+    p_off = eb_off + up((size_t)Np * 4);
+    const size_t part = Kp > kChunkSlabs * OK16 ? (size_t)Mp * Np * 8 : 0;
+    total = p_off + up(part) + 256;
+  }
+};
+
+template <int S>
+bta_status launch_ozaki(const Gemm& g, uint8_t* ws, int32_t* status, cudaStream_t s) {
+  using Cfg = OzCfg<S>;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+  BTA_TRY(tensor_map_encoder(&enc));
+  const int M = g.M, N = g.N, K = g.K;
+  const OzLayout L(M, N, K, S);
+  __nv_bfloat16* YA = reinterpret_cast<__nv_bfloat16*>(ws + L.a_off);
+  __nv_bfloat16* YB = reinterpret_cast<__nv_bfloat16*>(ws + L.b_off);
+  int* exA = reinterpret_cast<int*>(ws + L.ea_off);
+  int* exB = reinterpret_cast<int*>(ws + L.eb_off);
+  // rows of op(B)^T: Y[n][k] = op(B)[k][n]; the triangle flips with the transpose
+  const int trib = g.triB == TRI_LOWER ? TRI_UPPER : g.triB == TRI_UPPER ? TRI_LOWER : TRI_NONE;
+  // op(B)^T == op(A) (the symmetric update L L^T): one set of slices serves both
+  const bool same = g.A == g.B && g.lda == g.ldb && g.transA == !g.transB && g.triA == trib &&
+                    M == N;
+  SplitArgs sa;
+  sa.K = K;
+  sa.Kp = L.Kp;
+  sa.op[0] = {g.A, g.lda, g.transA, g.triA, M, L.Mp, exA, YA};
+  sa.op[1] = {g.B, g.ldb, !g.transB, trib, N, L.Np, exB, YB};
+  const int nops = same ? 1 : 2;
+  BTA_CUDA_TRY(cudaMemsetAsync(exA, 0, (size_t)L.Mp * 4, s));
+  if (!same) BTA_CUDA_TRY(cudaMemsetAsync(exB, 0, (size_t)L.Np * 4, s));
+  ozaki_exp_kernel<<<dim3(cdiv(K, 64), cdiv(std::max(M, N), 32), nops), 256, 0, s>>>(sa);
+  BTA_LAUNCHED();
+  ozaki_split_kernel<S><<<dim3(cdiv(L.Kp, 64), std::max(L.Mp, L.Np) / 32, nops), 256, 0, s>>>(sa);
+  BTA_LAUNCHED();
+  const __nv_bfloat16* YBm = same ? YA : YB;
+  const int bpitch = same ? L.Mp : L.Np;   // rows per B slice in its array
+  CUtensorMap mA, mB;
+  BTA_TRY(make_map_bf16(enc, &mA, YA, S * L.Mp, L.Kp, OM));
+  BTA_TRY(make_map_bf16(enc, &mB, YBm, S * bpitch, L.Kp, OBN));
+  static bool attr_set = false;
+  if (!attr_set) {
+    BTA_CUDA_TRY(cudaFuncSetAttribute(ozaki_gemm_kernel<S>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem));
+    attr_set = true;
+  }
+  OzArgs a;
+  a.M = M; a.N = N; a.Kp = L.Kp; a.Mp = L.Mp; a.Np = bpitch;
+  a.alpha = g.alpha; a.beta = g.beta; a.C = g.C; a.ldc = g.ldc;
+  a.Cin = g.Cin ? g.Cin : g.C; a.ldcin = g.Cin ? g.ldcin : g.ldc;
+  a.out_lower = g.out_lower; a.exA = exA; a.exB = same ? exA : exB; a.status = status;
+  a.partial = reinterpret_cast<long long*>(ws + L.p_off);
+  ozaki_gemm_kernel<S><<<dim3(L.Mp / OM, L.Np / OBN), kOzThreads, Cfg::kSmem, s>>>(mA, mB, a);
+  BTA_LAUNCHED();
+  return BTA_OK;
+}
+
+}  // namespace
+
+size_t ozaki_ws_bytes(int M, int N, int K, int slices) {
+  return OzLayout(M, N, K, slices).total;
+}
+
+bool ozaki_supported(const Gemm& g) {
+  return g.batch == 1 && !g.Ab && g.A && g.B && g.C && g.K >= 1 && g.K <= kMaxOzK && g.M >= 1 &&
+         g.N >= 1;
+}
+
+bta_status ozaki_gemm(const Gemm& g, void* ws, int32_t* status, int slices, cudaStream_t s) {
+  if (g.M <= 0 || g.N <= 0) return BTA_OK;
+  if (!ozaki_supported(g) || !ws) return BTA_ERR_ARG;
+  uint8_t* w = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(ws) + 255) &
+                                          ~(uintptr_t)255);
+  switch (slices) {
+    case 6: return launch_ozaki<6>(g, w, status, s);
+    case 7: return launch_ozaki<7>(g, w, status, s);
+    case 8: return launch_ozaki<8>(g, w, status, s);
+    default: return BTA_ERR_ARG;
+  }
+}
+
+}  // namespace bta

@@ -235,11 +235,12 @@ inline const double* const* cp(const std::vector<double*>& v) {
   return reinterpret_cast<const double* const*>(v.data());
 }
 
-// A b x b product of the sweep over the items idx: batched FP64, or one
-// split-precision tensor-core product per matrix.
+// A b x b product of the sweep over the items idx: batched FP64
+// (precision 0), or one tensor-core product per matrix: split TF32
+// (precision 1) or FP64 emulated from 8 BF16 slices (precision 2).
 bta_status big_product(const Gemm& g, const SweepItem* it, const std::vector<int>& idx,
                        int precision, cudaStream_t s) {
-  if (precision == 0) return gemm_f64(g, s);
+  if (precision == 0 || (precision == 2 && g.K > 5120)) return gemm_f64(g, s);
   for (size_t z = 0; z < idx.size(); ++z) {
     const SweepWs& ws = it[idx[z]].ws;
     if (!ws.tc) return BTA_ERR_ARG;
@@ -248,7 +249,11 @@ bta_status big_product(const Gemm& g, const SweepItem* it, const std::vector<int
     one.Ab = nullptr; one.Bb = nullptr; one.Cb = nullptr; one.Cinb = nullptr;
     one.A = g.Ab[z]; one.B = g.Bb[z]; one.C = g.Cb[z];
     one.Cin = g.Cinb ? g.Cinb[z] : g.Cb[z];
-    BTA_TRY(tc_gemm_mixed(one, ws.tc, ws.tcstat, s));
+    if (precision == 2) {
+      BTA_TRY(ozaki_gemm(one, ws.tc, ws.tcstat, 8, s));
+    } else {
+      BTA_TRY(tc_gemm_mixed(one, ws.tc, ws.tcstat, s));
+    }
   }
   return BTA_OK;
 }

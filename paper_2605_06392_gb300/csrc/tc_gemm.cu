@@ -25,9 +25,12 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace bta {
 namespace {
+
+using namespace tc;
 
 constexpr int TM = 128, TN = 128, TK = 32;          // tile rows, cols, fp32 per K slab
 constexpr int kStages = 3;
@@ -37,46 +40,6 @@ constexpr int kTcThreads = 128;
 constexpr int kSmemBytes = kStages * kStageBytes + 1024 + 128;
 constexpr uint32_t kTmemCols = 128;                 // 128 lanes x 128 fp32 columns
 constexpr long long kWaitLimit = 1ll << 21;          // bounded mbarrier polls (~1 s)
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t addr, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t addr, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(addr), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t addr, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(addr), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait; false when the limit expired.
-__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
-  for (long long it = 0; it < kWaitLimit; ++it)
-    if (mbar_try_wait(addr, parity)) return true;
-  return false;
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t mbar,
-                                            int x, int y) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(mbar), "r"(x), "r"(y)
-      : "memory");
-}
 
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle,
 // 8-row groups 1024 bytes apart.
@@ -101,29 +64,6 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, 
       " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
       "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
       : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t mbar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
-      : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
-      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-        "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int j = 0; j < 32; ++j) v[j] = __uint_as_float(r[j]);
 }
 
 struct TcArgs {
@@ -181,7 +121,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     for (int kt = 0; kt < nk; ++kt) {
       const int s = kt % kStages;
       if (kt >= kStages &&
-          !mbar_wait(smem_u32(&bars[kStages + s]), (uint32_t)((kt / kStages - 1) & 1))) {
+          !mbar_wait(smem_u32(&bars[kStages + s]), (uint32_t)((kt / kStages - 1) & 1), kWaitLimit)) {
         s_abort = 1;
         break;
       }
@@ -200,7 +140,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     int issued = 0;
     for (int kt = 0; kt < nk; ++kt) {
       const int s = kt % kStages;
-      if (!mbar_wait(smem_u32(&bars[s]), (uint32_t)((kt / kStages) & 1))) {
+      if (!mbar_wait(smem_u32(&bars[s]), (uint32_t)((kt / kStages) & 1), kWaitLimit)) {
         s_abort = 1;
         break;
       }
@@ -222,7 +162,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
   __syncwarp();
   // ---- epilogue: all four warps (the decision below is uniform per CTA)
-  const bool done = mbar_wait(smem_u32(&bars[2 * kStages]), 0);
+  const bool done = mbar_wait(smem_u32(&bars[2 * kStages]), 0, kWaitLimit);
   const int failed = __syncthreads_or(!done || s_abort);
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (failed) {
@@ -288,19 +228,8 @@ __global__ void split_tf32_kernel(int rows, int K, int Kp, const double* __restr
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
-std::mutex g_encode_mu;
 
-bta_status get_encode() {
-  std::lock_guard<std::mutex> lock(g_encode_mu);
-  if (g_encode) return BTA_OK;
-  cudaDriverEntryPointQueryResult q;
-  void* fn = nullptr;
-  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
-                                                   cudaEnableDefault, &q);
-  if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return BTA_ERR_CUDA;
-  g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-  return BTA_OK;
-}
+bta_status get_encode() { return tensor_map_encoder(&g_encode); }
 
 // 2D map over a row-major fp32 array rows x Kp, box 32 (K) x 128 (rows).
 bta_status make_map(CUtensorMap* map, const float* base, int rows, int Kp) {
@@ -316,6 +245,22 @@ bta_status make_map(CUtensorMap* map, const float* base, int rows, int Kp) {
 }
 
 }  // namespace
+
+bta_status tensor_map_encoder(PFN_cuTensorMapEncodeTiled_v12000* out) {
+  static std::mutex mu;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                                     cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !p) return BTA_ERR_CUDA;
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  *out = fn;
+  return BTA_OK;
+}
 
 size_t tc_gemm_ws_bytes(int M, int N, int K) {
   const size_t Kp = (size_t)(K + 3) / 4 * 4;
