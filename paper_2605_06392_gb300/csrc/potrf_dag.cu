@@ -10,11 +10,14 @@
 //
 // Tasks, for step k = 0..p-1 (A's lower tiles are reused in place: first the
 // trailing matrix W, then the inverse's accumulator R, then the inverse X):
-//   F(k)      leaf on W_kk: D / unit-L elimination with its inverse
-//             -> X_kk = L_kk^{-1} into A_kk, log-det slot k
-//   S(i,k)    L_ik = W_ik X_kk^T                     (into the scratch Lt)
+//   H         the chain, one task per block run by one CTA: for c = 0..p-1,
+//             L_{c,c-1} = W_{c,c-1} X_{c-1,c-1}^T, W_cc -= L L^T, and the leaf
+//             on W_cc (D / unit-L elimination with its inverse) -> X_cc =
+//             L_cc^{-1} into A_cc, log-det slot c; X_cc stays in shared
+//             memory for the next step
+//   S(i,k)    L_ik = W_ik X_kk^T, i >= k+2           (into the scratch Lt)
 //   G(k,j)    X_kj = X_kk R_kj            (j < k; R_kj = -sum_m L_km X_mj)
-//   U(i,j,k)  W_ij -= L_ik L_jk^T         (k < j <= i; column k+1 first)
+//   U(i,j,k)  W_ij -= L_ik L_jk^T         (k < j <= i, not (k+1,k+1); column k+1 first)
 //   V(i,j,k)  R_ij -= L_ik X_kj           (k < i, j <= k; R_ij = -L_ij X_jj at k = j)
 // A task waits only for tasks earlier in the list, which running CTAs hold,
 // so the graph always drains.  Per-tile counters (W updates applied, R
@@ -39,7 +42,7 @@ constexpr int kMaxP = 160;              // tile rows supported (ld <= 5120)
 constexpr unsigned long long kWaitNs = 2000000000ull;
 constexpr int32_t kFailTimeout = 0x40000000;
 
-enum : int { TK_F = 0, TK_S = 1, TK_G = 2, TK_U = 3, TK_V = 4, TK_C = 5 };
+enum : int { TK_H = 0, TK_S = 1, TK_G = 2, TK_U = 3, TK_V = 4 };
 
 struct DagInst {
   double* A;       // n x n block, ld
@@ -55,7 +58,7 @@ struct DagArgs {
   int total;                // tasks over all instances
   int* counter;             // global task ticket
   int* abort;               // shared abort flag
-  int* smbusy;              // per SM: chain tasks running there (see TK_C)
+  int* smbusy;              // per SM: chain tasks running there (see TK_H)
   int yield;                // bulk tasks wait while a chain task holds their SM
   int off[kMaxP + 1];       // task offset of each step within one instance
   DagInst inst[kMaxBatch];
@@ -138,6 +141,51 @@ __device__ __forceinline__ void tile_mm(double (*X)[T + 1], double (*Y)[T + 1], 
   }
 }
 
+// out[r][c] = sum_{m <= c} W[r][m] Y[c][m] = (W Y^T)[r][c] for lower-triangular Y
+// (its upper part is not read).  Same thread layout as tile_mm; the m range
+// of a thread's columns (ty, ty + 16) is uniform within a warp, so the
+// skipped half of the products issues no instructions.
+__device__ __forceinline__ void tile_mm_lt(double (*W)[T + 1], double (*Y)[T + 1],
+                                           double (*out)[T + 1]) {
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double a00 = 0.0, a01 = 0.0, a10 = 0.0, a11 = 0.0;
+  for (int m = 0; m <= ty; ++m) {
+    const double x0 = W[tx][m], x1 = W[tx + 16][m];
+    const double y0 = Y[ty][m], y1 = Y[ty + 16][m];
+    a00 = fma(x0, y0, a00); a01 = fma(x0, y1, a01);
+    a10 = fma(x1, y0, a10); a11 = fma(x1, y1, a11);
+  }
+  for (int m = ty + 1; m <= ty + 16; ++m) {
+    const double y1 = Y[ty + 16][m];
+    a01 = fma(W[tx][m], y1, a01);
+    a11 = fma(W[tx + 16][m], y1, a11);
+  }
+  out[tx][ty] = a00; out[tx][ty + 16] = a01;
+  out[tx + 16][ty] = a10; out[tx + 16][ty + 16] = a11;
+}
+
+// W[r][c] -= sum_m L[r][m] L[c][m] on the lower triangle (r >= c): threads
+// 0..135 each own one 2 x 2 block of the 16 x 16 block triangle, so only 5
+// of the 8 warps issue FMAs.  Upper entries of diagonal blocks get the same
+// update (W is symmetric; only its lower part is read afterwards).
+__device__ __forceinline__ void tile_syrk_lower(double (*L)[T + 1], double (*W)[T + 1]) {
+  const int b = threadIdx.x;
+  if (b >= 136) return;
+  int bi = 0;
+  while ((bi + 1) * (bi + 2) / 2 <= b) ++bi;
+  const int bj = b - bi * (bi + 1) / 2;
+  const int r = 2 * bi, c = 2 * bj;
+  double a00 = 0.0, a01 = 0.0, a10 = 0.0, a11 = 0.0;
+#pragma unroll 8
+  for (int m = 0; m < T; ++m) {
+    const double x0 = L[r][m], x1 = L[r + 1][m], y0 = L[c][m], y1 = L[c + 1][m];
+    a00 = fma(x0, y0, a00); a01 = fma(x0, y1, a01);
+    a10 = fma(x1, y0, a10); a11 = fma(x1, y1, a11);
+  }
+  W[r][c] -= a00; W[r][c + 1] -= a01;
+  W[r + 1][c] -= a10; W[r + 1][c + 1] -= a11;
+}
+
 struct Task {
   int type, i, j, k;
 };
@@ -145,19 +193,17 @@ struct Task {
 // Number of tasks of step k (see potrf_dag_batch for the list order).
 __host__ __device__ inline int step_tasks(int p, int k) {
   const int nS = p - 2 - k > 0 ? p - 2 - k : 0;
-  const int nC = k + 1 < p ? 1 : 0;
-  const int nU = (p - 1 - k) * (p - k) / 2 - nC;
+  const int nU = (p - 1 - k) * (p - k) / 2 - (k + 1 < p ? 1 : 0);
   const int nV = (p - 1 - k) * (k + 1);
-  return nS + nC + k + nU + nV;
+  return nS + k + nU + nV;
 }
 
-// Decode task index l of one instance.  Index 0 is F(0); then for each step
-// k: S(i,k) for i >= k+2, the fused chain task C(k+1) = S(k+1,k) +
-// U(k+1,k+1,k) + F(k+1), G(k,j), the remaining U(i,j,k) (column k+1 first),
-// and V(i,j,k).
+// Decode task index l of one instance.  Index 0 is the chain H; then for
+// each step k: S(i,k) for i >= k+2, G(k,j), U(i,j,k) (column k+1 first,
+// without (k+1,k+1), which the chain applies) and V(i,j,k).
 __device__ Task decode(const DagArgs& g, int l) {
   const int p = g.p;
-  Task t{TK_F, 0, 0, 0};
+  Task t{TK_H, 0, 0, 0};
   if (l == 0) return t;
   l -= 1;
   int lo = 0, hi = p - 1;
@@ -171,10 +217,6 @@ __device__ Task decode(const DagArgs& g, int l) {
   const int nS = p - 2 - k > 0 ? p - 2 - k : 0;
   if (r < nS) { t.type = TK_S; t.i = k + 2 + r; t.j = k; return t; }
   r -= nS;
-  if (k + 1 < p) {
-    if (r == 0) { t.type = TK_C; t.i = k + 1; t.j = k + 1; return t; }
-    r -= 1;
-  }
   if (r < k) { t.type = TK_G; t.i = k; t.j = r; return t; }
   r -= k;
   const int nU = (p - 1 - k) * (p - k) / 2 - (k + 1 < p ? 1 : 0);
@@ -191,94 +233,181 @@ __device__ Task decode(const DagArgs& g, int l) {
   return t;
 }
 
-// 1 / v by Newton-Raphson (r <- r + r (1 - v r), each step doubling the
-// correct bits) from the FP32 reciprocal: two steps reach FP64 accuracy with
-// 4 dependent FP64 operations, where a division costs about ten on the
-// leaf's serial chain.  Values outside FP32's range use the division.
+// 1 / v to FP64 accuracy.  Seed: the FP32 reciprocal of v's leading bits,
+// with v narrowed and the result widened by integer operations (a GB300 FP64
+// instruction, conversions included, has ~64 clock cycles of latency).  With
+// r = (1 + eps) / v, e = 1 - v r = -eps, the correction r (1 + e + e^2) has
+// relative error eps^3 (~2^-66) plus rounding: three dependent FP64 FMAs.
+// Values outside the seed's exponent range use the division.
 __device__ __forceinline__ double recip(double v) {
-  const double av = fabs(v);
-  if (!(av > 1e-30 && av < 1e30)) return 1.0 / v;
-  double r = (double)__frcp_rn((float)v);
-  double e = fma(-v, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-v, r, 1.0);
-  return fma(r, e, r);
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e < 1023 - 100 || e > 1023 + 100) return 1.0 / v;
+  const unsigned f = (unsigned)((b >> 32) & 0x80000000u) | ((unsigned)(e - 1023 + 127) << 23) |
+                     (unsigned)((b >> 29) & 0x7FFFFFu);
+  float rf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(__uint_as_float(f)));
+  const unsigned rb = __float_as_uint(rf);
+  const unsigned long long db = ((unsigned long long)(rb & 0x80000000u) << 32) |
+                                ((unsigned long long)(((rb >> 23) & 0xFF) - 127 + 1023) << 52) |
+                                ((unsigned long long)(rb & 0x7FFFFFu) << 29);
+  const double r = __longlong_as_double((long long)db);
+  const double err = fma(-v, r, 1.0);
+  return fma(r, fma(err, err, err), r);
 }
 
-// Leaf on smem tile S (lower, W_kk): writes X_kk = L_kk^{-1} into Xo, returns
-// log det in *ld (thread 0) and a bad-pivot flag.  (Same elimination as the
-// standalone leaf kernel, with 256 threads.)
-__device__ void leaf(double (*S)[T + 1], double (*X)[T + 1], double* lcol, double* rinv,
-                     double* logdet, int* bad) {
-  constexpr int kPos = T * (T + 1) / 2;
-  constexpr int kPer = (kPos + kDagThreads - 1) / kDagThreads;
-  const int tid = threadIdx.x;
+// d^{-1/2} to FP64 accuracy: FP32 seed of the narrowed value widened by
+// integer operations, then y (1 + e/2 + 3e^2/8) with e = 1 - d y^2 (relative
+// error ~e^3): five dependent FP64 operations.  Outside the seed's range the
+// library square root and division.
+__device__ __forceinline__ double rsqrt_fp64(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (!(d > 0.0) || e < 1023 - 100 || e > 1023 + 100) return 1.0 / sqrt(d);
+  const unsigned f = ((unsigned)(e - 1023 + 127) << 23) | (unsigned)((b >> 29) & 0x7FFFFFu);
+  float yf;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(__uint_as_float(f)));
+  const unsigned rb = __float_as_uint(yf);
+  const unsigned long long db = ((unsigned long long)(((rb >> 23) & 0xFF) - 127 + 1023) << 52) |
+                                ((unsigned long long)(rb & 0x7FFFFFu) << 29);
+  const double y = __longlong_as_double((long long)db);
+  const double err = fma(-d, y * y, 1.0);
+  return fma(y, fma(0.375, err, 0.5) * err, y);
+}
+
+// Leaf on smem tile S (lower, W_kk): D / unit-L elimination carrying the
+// inverse of the unit-L factor in X, then X = D^{-1/2} (unit L)^{-1} =
+// L_kk^{-1}; the pivots d_i stay in piv[] (leaf_logdet sums their logs, off
+// the critical path).
+//
+// Pivot j eliminates column j with the multipliers l_ij = S_ij / d_j:
+// S_ik -= l_ij S_kj (j < k <= i) and X_ik -= l_ij X_jk (k <= j < i).  Warp 0
+// runs one pivot ahead: while warps 1-3 and 5-7 apply pivot j to columns
+// k >= j+2 and to X, it applies pivot j to column j+1, takes d_{j+1}, its
+// reciprocal and the next multipliers, so each pivot costs one barrier and
+// the serial chain per pivot is one FMA, the reciprocal and one multiply.
+// Warp 4 shares warp 0's scheduler and FP64 unit and stays idle, so the
+// chain's instructions do not queue behind bulk ones.
+__device__ void leaf(double (*S)[T + 1], double (*X)[T + 1], double (*lcol)[T], double* piv,
+                     double* rs) {
+  constexpr int kPos = T * (T + 1) / 2;   // lower-triangle positions, row by row
+  constexpr int kBulk = kDagThreads - 64;   // warps 1-3 and 5-7
+  constexpr int kPer = (kPos + kBulk - 1) / kBulk;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool bulk = warp != 0 && warp != 4;
+  const int bt = warp < 4 ? tid - 32 : tid - 64;   // 0..kBulk-1 over the bulk warps
   int pi[kPer], pk[kPer];
+  if (bulk) {
 #pragma unroll
-  for (int r = 0; r < kPer; ++r) {
-    const int q = tid + kDagThreads * r;
-    if (q < kPos) {
-      int i = 0;
-      while ((i + 1) * (i + 2) / 2 <= q) ++i;
-      pi[r] = i;
-      pk[r] = q - i * (i + 1) / 2;
-    } else {
-      pi[r] = -1;
-      pk[r] = 0;
+    for (int r = 0; r < kPer; ++r) {
+      const int q = bt + kBulk * r;
+      if (q < kPos) {
+        int i = 0;
+        while ((i + 1) * (i + 2) / 2 <= q) ++i;
+        pi[r] = i;
+        pk[r] = q - i * (i + 1) / 2;
+      } else {
+        pi[r] = -1;
+        pk[r] = 0;
+      }
     }
   }
   for (int e = tid; e < T * T; e += kDagThreads) X[e % T][e / T] = (e % T == e / T) ? 1.0 : 0.0;
-  if (tid == 0) rinv[0] = recip(S[0][0]);
+  if (tid < 32) {   // pivot 0 and its multipliers
+    const double d = S[0][0];
+    const double r = recip(d);
+    if (lane > 0) lcol[0][lane] = S[lane][0] * r;
+    if (lane == 0) piv[0] = d;
+  }
   __syncthreads();
-  for (int j = 0; j < T; ++j) {
-    if (tid > j && tid < T) lcol[tid] = S[tid][j] * rinv[j];
-    __syncthreads();
+  for (int j = 0; j < T - 1; ++j) {
+    const double* lj = lcol[j & 1];
+    if (tid < 32) {
+      // column j+1 with pivot j, then pivot j+1 and its multipliers
+      const int c = j + 1;
+      double v = 0.0;
+      if (lane >= c) {
+        v = fma(-lj[lane], S[c][j], S[lane][c]);
+        S[lane][c] = v;
+      }
+      const double d = __shfl_sync(0xffffffffu, v, c);
+      const double r = recip(d);
+      if (lane > c) lcol[c & 1][lane] = v * r;
+      if (lane == 0) piv[c] = d;
+    } else if (bulk) {
+      // k > j+1: trailing S_ik -= l_ij S_kj; k <= j: X_ik -= l_ij X_jk.  The
+      // positions are distinct and none is a source of this pivot (column j of
+      // S, row j of X), so all loads go first and the FMAs overlap.
+      double* dst[kPer];
+      double dv[kPer], sv[kPer], lv[kPer];
+      bool act[kPer];
 #pragma unroll
-    for (int r = 0; r < kPer; ++r) {
-      const int i = pi[r], k = pk[r];
-      if (i > j) {
-        const double lij = lcol[i];
-        if (k > j) {
-          const double v = fma(-lij, S[k][j], S[i][k]);
-          S[i][k] = v;
-          if (i == j + 1 && k == j + 1) rinv[j + 1] = recip(v);
-        } else {
-          X[i][k] = fma(-lij, X[j][k], X[i][k]);
+      for (int q = 0; q < kPer; ++q) {
+        const int i = pi[q], k = pk[q];
+        act[q] = i > j && k != j + 1;
+        if (act[q]) {
+          dst[q] = k > j ? &S[i][k] : &X[i][k];
+          sv[q] = k > j ? S[k][j] : X[j][k];
+          dv[q] = *dst[q];
+          lv[q] = lj[i];
         }
       }
+#pragma unroll
+      for (int q = 0; q < kPer; ++q)
+        if (act[q]) *dst[q] = fma(-lv[q], sv[q], dv[q]);
     }
     __syncthreads();
   }
-  if (tid < T) rinv[tid] = 1.0 / sqrt(S[tid][tid]);
+  if (tid < 32) rs[tid] = rsqrt_fp64(piv[tid]);   // rows scale by d_i^{-1/2}
   __syncthreads();
   for (int e = tid; e < T * T; e += kDagThreads) {
     const int i = e % T, k = e / T;
-    X[i][k] = i >= k ? X[i][k] * rinv[i] : 0.0;
+    X[i][k] = i >= k ? X[i][k] * rs[i] : 0.0;
   }
-  if (tid < 32) {
-    const double dj = S[tid][tid];
+  __syncthreads();
+}
+
+// Log-det slot of a leaf: sum of log d_i over its pivots, and the failure
+// code on a non-positive or non-finite pivot (warp 0).
+__device__ __forceinline__ void leaf_logdet(const double* piv, double* slot, int32_t* fail,
+                                            int32_t code) {
+  if (threadIdx.x < 32) {
+    const double dj = piv[threadIdx.x];
     const bool b = !(dj > 0.0) || !isfinite(dj);
     double l = b ? 0.0 : log(dj);
 #pragma unroll
     for (int o = 16; o; o >>= 1) l += __shfl_xor_sync(0xffffffffu, l, o);
     const unsigned anyb = __ballot_sync(0xffffffffu, b);
-    if (tid == 0) {
-      *logdet = l;
-      *bad = anyb != 0;
+    if (threadIdx.x == 0) {
+      *slot = l;
+      if (anyb) atomicCAS(fail, -1, code);
     }
   }
-  __syncthreads();
 }
 
 __global__ void __launch_bounds__(kDagThreads) potrf_dag_kernel(DagArgs g) {
   __shared__ double S0[T][T + 1], S1[T][T + 1], S2[T][T + 1], S3[T][T + 1];
-  __shared__ double lcol[T], rinv[T];
+  __shared__ double lcol[2][T], piv[T], rs[T];
   __shared__ int s_task, s_ok;
-  __shared__ double s_logdet;
-  __shared__ int s_bad;
   const int p = g.p, ld = g.ld, pp = p * p;
+  int* busy = &g.smbusy[sm_id() & 255];
   while (true) {
-    if (threadIdx.x == 0) s_task = atomicAdd(g.counter, 1);
+    if (threadIdx.x == 0) {
+      // On an SM that runs a chain, take no task while the chain is there: it
+      // gets the SM's whole FP64 pipe.  Waiting before taking a ticket holds
+      // nothing another task needs.
+      if (g.yield && ld_acquire(busy) > 0) {
+        const unsigned long long t0 = now_ns();
+        while (ld_acquire(busy) > 0 && ld_acquire(g.counter) < g.total && !ld_acquire(g.abort)) {
+          __nanosleep(256);
+          if (now_ns() - t0 > kWaitNs) {
+            atomicExch(g.abort, 1);
+            break;
+          }
+        }
+      }
+      s_task = atomicAdd(g.counter, 1);
+    }
     __syncthreads();
     const int tg = s_task;
     __syncthreads();
@@ -292,16 +421,55 @@ __global__ void __launch_bounds__(kDagThreads) potrf_dag_kernel(DagArgs g) {
     int* doneS = doneF + p;
     int* doneG = doneS + pp;
     auto Lt = [&](int i, int k) { return I.Lt + ((int64_t)i * (i - 1) / 2 + k) * T * T; };
-    // ---- wait for the tiles this task reads
+    if (t.type == TK_H) {
+      // ---- the chain: every diagonal step of this block on this CTA
+      if (threadIdx.x == 0 && g.yield) atomicAdd(busy, 1);
+      for (int c = 0; c < p; ++c) {
+        if (c > 0) {
+          // W_{c,c-1} and W_cc updated through step c-2 by the U tasks
+          if (threadIdx.x == 0)
+            s_ok = wait_ge(&cntW[c * p + c - 1], c - 1, g.abort) &&
+                   wait_ge(&cntW[c * p + c], c - 1, g.abort);
+          __syncthreads();
+          if (!s_ok) {
+            if (threadIdx.x == 0) {
+              atomicCAS(I.fail, -1, kFailTimeout);
+              if (g.yield) atomicSub(busy, 1);
+            }
+            return;
+          }
+          load_tile(S0, tile(I.A, ld, c, c - 1), ld);
+          load_tile(S3, tile(I.A, ld, c, c), ld);
+          __syncthreads();
+          tile_mm_lt(S0, S1, S2);                 // L_{c,c-1} = W X_{c-1,c-1}^T (S1)
+          __syncthreads();
+          store_tile(Lt(c, c - 1), T, S2, false);
+          __syncthreads();
+          if (threadIdx.x == 0) { __threadfence(); st_release(&doneS[c * p + c - 1], 1); }
+          tile_syrk_lower(S2, S3);                // W_cc -= L L^T (lower)
+          __syncthreads();
+        } else {
+          load_tile(S3, tile(I.A, ld, 0, 0), ld);
+          __syncthreads();
+        }
+        leaf(S3, S1, lcol, piv, rs);              // S1 = X_cc = L_cc^{-1}
+        store_tile(tile(I.A, ld, c, c), ld, S1, true);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          __threadfence();
+          st_release(&cntW[c * p + c], c);
+          st_release(&doneF[c], 1);
+        }
+        leaf_logdet(piv, &I.slots[c], I.fail, I.code);   // after the release: off the chain
+        __syncthreads();
+      }
+      if (threadIdx.x == 0 && g.yield) atomicSub(busy, 1);
+      continue;
+    }
+    // ---- bulk task: wait for the tiles it reads
     if (threadIdx.x == 0) {
       bool ok = true;
       switch (t.type) {
-        case TK_F: ok = wait_ge(&cntW[t.k * p + t.k], t.k, g.abort); break;
-        case TK_C:   // t.i = k + 1 = c: W_{c,c-1} and W_cc up to step c-2 here;
-                     // F(c-1) is awaited after these tiles are loaded
-          ok = wait_ge(&cntW[t.i * p + t.i - 1], t.i - 1, g.abort) &&
-               wait_ge(&cntW[t.i * p + t.i], t.i - 1, g.abort);
-          break;
         case TK_S:
           ok = wait_ge(&doneF[t.k], 1, g.abort) && wait_ge(&cntW[t.i * p + t.k], t.k, g.abort);
           break;
@@ -320,20 +488,6 @@ __global__ void __launch_bounds__(kDagThreads) potrf_dag_kernel(DagArgs g) {
                            : wait_ge(&doneG[t.k * p + t.j], 1, g.abort)) &&
                wait_ge(&cntR[t.i * p + t.j], t.k - t.j, g.abort);
       }
-      // A bulk task starts only when no chain task holds this SM, so the chain
-      // (the latency-critical path) gets the SM's whole FP64 pipe.
-      if (ok && g.yield && t.type != TK_C && t.type != TK_F) {
-        const int* busy = &g.smbusy[sm_id() & 255];
-        if (ld_acquire(busy) > 0) {
-          const unsigned long long t0 = now_ns();
-          while (ld_acquire(busy) > 0) {
-            __nanosleep(128);
-            if (ld_acquire(g.abort)) { ok = false; break; }
-            if (now_ns() - t0 > kWaitNs) { atomicExch(g.abort, 1); ok = false; break; }
-          }
-        }
-      }
-      if (ok && t.type == TK_C && g.yield) atomicAdd(&g.smbusy[sm_id() & 255], 1);
       s_ok = ok;
       if (!ok) atomicCAS(I.fail, -1, kFailTimeout);
     }
@@ -341,68 +495,11 @@ __global__ void __launch_bounds__(kDagThreads) potrf_dag_kernel(DagArgs g) {
     if (!s_ok) return;
     // ---- execute
     switch (t.type) {
-      case TK_F: {
-        load_tile(S0, tile(I.A, ld, t.k, t.k), ld);
-        __syncthreads();
-        leaf(S0, S1, lcol, rinv, &s_logdet, &s_bad);
-        store_tile(tile(I.A, ld, t.k, t.k), ld, S1, true);
-        if (threadIdx.x == 0) {
-          I.slots[t.k] = s_logdet;
-          if (s_bad) atomicCAS(I.fail, -1, I.code);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) { __threadfence(); st_release(&doneF[t.k], 1); }
-        break;
-      }
-      case TK_C: {   // c = t.i: L_{c,c-1}, W_cc -= L L^T, then the leaf of W_cc
-        const int c = t.i;
-        load_tile(S0, tile(I.A, ld, c, c - 1), ld);
-        load_tile(S3, tile(I.A, ld, c, c), ld);
-        if (threadIdx.x == 0) s_ok = wait_ge(&doneF[c - 1], 1, g.abort);
-        __syncthreads();
-        if (!s_ok) {
-          if (threadIdx.x == 0) {
-            atomicCAS(I.fail, -1, kFailTimeout);
-            if (g.yield) atomicSub(&g.smbusy[sm_id() & 255], 1);
-          }
-          return;
-        }
-        load_tile(S1, tile(I.A, ld, c - 1, c - 1), ld);
-        __syncthreads();
-        for (int e = threadIdx.x; e < T * T; e += kDagThreads)
-          if (e % T < e / T) S1[e % T][e / T] = 0.0;
-        __syncthreads();
-        tile_mm(S0, S1, true, S2, 1.0, false);            // S2 = L_{c,c-1}
-        __syncthreads();
-        store_tile(Lt(c, c - 1), T, S2, false);
-        __syncthreads();
-        if (threadIdx.x == 0) { __threadfence(); st_release(&doneS[c * p + c - 1], 1); }
-        tile_mm(S2, S2, true, S3, -1.0, true);            // W_cc -= L L^T
-        __syncthreads();
-        leaf(S3, S1, lcol, rinv, &s_logdet, &s_bad);
-        store_tile(tile(I.A, ld, c, c), ld, S1, true);
-        if (threadIdx.x == 0) {
-          I.slots[c] = s_logdet;
-          if (s_bad) atomicCAS(I.fail, -1, I.code);
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-          __threadfence();
-          st_release(&cntW[c * p + c], c);
-          st_release(&doneF[c], 1);
-          if (g.yield) atomicSub(&g.smbusy[sm_id() & 255], 1);
-        }
-        break;
-      }
       case TK_S: {   // L_ik = W_ik X_kk^T
         load_tile(S0, tile(I.A, ld, t.i, t.k), ld);
         load_tile(S1, tile(I.A, ld, t.k, t.k), ld);
         __syncthreads();
-        // X_kk is lower: zero its upper part before use
-        for (int e = threadIdx.x; e < T * T; e += kDagThreads)
-          if (e % T < e / T) S1[e % T][e / T] = 0.0;
-        __syncthreads();
-        tile_mm(S0, S1, true, S2, 1.0, false);
+        tile_mm_lt(S0, S1, S2);                   // X_kk lower: its upper part is not read
         __syncthreads();
         store_tile(Lt(t.i, t.k), T, S2, false);
         __syncthreads();
