@@ -210,8 +210,11 @@ struct OzArgs {
   int32_t* status;
 };
 
+// At most 248 registers a thread: with a task-graph factor CTA of the other
+// sweep (256 threads x 68 registers, ~26 KB) the CTA still fits on one SM
+// (64 K registers, 228 KB), so the two overlap on the FP64 and tensor pipes.
 template <int S>
-__global__ void __launch_bounds__(kOzThreads, 1)
+__global__ void __maxnreg__(248)
     ozaki_gemm_kernel(const __grid_constant__ CUtensorMap mA,
                       const __grid_constant__ CUtensorMap mB, OzArgs g) {
   using Cfg = OzCfg<S>;

@@ -386,7 +386,9 @@ __device__ __forceinline__ void leaf_logdet(const double* piv, double* slot, int
 }
 
 __global__ void __launch_bounds__(kDagThreads) potrf_dag_kernel(DagArgs g) {
-  __shared__ double S0[T][T + 1], S1[T][T + 1], S2[T][T + 1], S3[T][T + 1];
+  // three tiles (~26 KB with the leaf's vectors): a CTA fits beside a
+  // tensor-core GEMM CTA of the other sweep on the same SM
+  __shared__ double S0[T][T + 1], S1[T][T + 1], S2[T][T + 1];
   __shared__ double lcol[2][T], piv[T], rs[T];
   __shared__ int s_task, s_ok;
   const int p = g.p, ld = g.ld, pp = p * p;
@@ -439,20 +441,34 @@ __global__ void __launch_bounds__(kDagThreads) potrf_dag_kernel(DagArgs g) {
             return;
           }
           load_tile(S0, tile(I.A, ld, c, c - 1), ld);
-          load_tile(S3, tile(I.A, ld, c, c), ld);
+          // W_cc into registers now, into S0 once the product has read it
+          double wcc[T * T / kDagThreads];
+          {
+            const double* src = tile(I.A, ld, c, c);
+#pragma unroll
+            for (int q = 0; q < T * T / kDagThreads; ++q) {
+              const int e = threadIdx.x + kDagThreads * q;
+              wcc[q] = __ldcg(src + (int64_t)(e / T) * ld + e % T);
+            }
+          }
           __syncthreads();
           tile_mm_lt(S0, S1, S2);                 // L_{c,c-1} = W X_{c-1,c-1}^T (S1)
           __syncthreads();
+#pragma unroll
+          for (int q = 0; q < T * T / kDagThreads; ++q) {
+            const int e = threadIdx.x + kDagThreads * q;
+            S0[e % T][e / T] = wcc[q];
+          }
           store_tile(Lt(c, c - 1), T, S2, false);
           __syncthreads();
           if (threadIdx.x == 0) { __threadfence(); st_release(&doneS[c * p + c - 1], 1); }
-          tile_syrk_lower(S2, S3);                // W_cc -= L L^T (lower)
+          tile_syrk_lower(S2, S0);                // W_cc -= L L^T (lower)
           __syncthreads();
         } else {
-          load_tile(S3, tile(I.A, ld, 0, 0), ld);
+          load_tile(S0, tile(I.A, ld, 0, 0), ld);
           __syncthreads();
         }
-        leaf(S3, S1, lcol, piv, rs);              // S1 = X_cc = L_cc^{-1}
+        leaf(S0, S1, lcol, piv, rs);              // S1 = X_cc = L_cc^{-1}
         store_tile(tile(I.A, ld, c, c), ld, S1, true);
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -557,13 +573,14 @@ __global__ void __launch_bounds__(kDagThreads) potrf_dag_kernel(DagArgs g) {
   }
 }
 
-// Resident CTAs per SM of the persistent grid: more CTAs keep SMs busy while
-// some wait on dependencies, fewer give the critical-path tiles a larger share
-// of each SM's FP64 pipe.  BTA_DAG_CTAS_PER_SM overrides the default.
+// Resident CTAs per SM of the persistent grid.  The kernel is bound by its
+// chain, and one CTA per SM (as fast as two, measured) leaves room on every
+// SM for a tensor-core GEMM CTA of the other sweep.  BTA_DAG_CTAS_PER_SM
+// overrides the default.
 int dag_ctas_per_sm() {
   static int v = [] {
     const char* e = getenv("BTA_DAG_CTAS_PER_SM");
-    int x = e ? atoi(e) : 2;
+    int x = e ? atoi(e) : 1;
     return x < 1 ? 1 : (x > 8 ? 8 : x);
   }();
   return v;
