@@ -264,6 +264,13 @@ bta_status run_group(inla_model* m, int mode, int cnt, int prec, int use_graph,
     for (auto& g : m->graphs)
       if (g.mode == mode && g.count == cnt && g.precision == prec) gk = &g;
     if (!gk) {
+      if (mode < 2) {
+        // one eager evaluation first: it times the tile shapes of the
+        // products the graph will hold, which then replays those choices
+        TuneScope tune;
+        BTA_TRY(record_group(m, mode, cnt, prec, stream));
+        BTA_CUDA_TRY(cudaStreamSynchronize(stream));
+      }
       const int64_t before = g_launches;
       cudaStream_t cap;
       BTA_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
@@ -742,6 +749,11 @@ bta_status inla_batch_value_and_grad(inla_batch* b, const double* theta, int32_t
     std::memcpy(m->htheta, theta + (size_t)i * ldt, m->d * sizeof(double));
   }
   if (!b->exec[g][prec]) {
+    {  // an eager run first times the products' tile shapes (see run_group)
+      TuneScope tune;
+      BTA_TRY(record_batch(b, g, prec, stream));
+      BTA_CUDA_TRY(cudaStreamSynchronize(stream));
+    }
     const int64_t before = g_launches;
     cudaStream_t cap;
     BTA_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));

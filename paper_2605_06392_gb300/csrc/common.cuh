@@ -135,6 +135,14 @@ constexpr int kGemvSplit = 16;      // K splits; work needs kGemvSplit * M doubl
 // gemm_f64 for a single problem; ws holds tc_gemm_ws_bytes(M, N, K) bytes;
 // *status (device, may be null) receives BTA_ERR_TIMEOUT if a bounded wait
 // inside the kernel expired.
+// While one is open on this thread, gemm_f64 times each not yet measured
+// product shape's tile candidates on scratch operands and keeps the fastest
+// (outside stream capture only).
+struct TuneScope {
+  TuneScope();
+  ~TuneScope();
+};
+
 bta_status tc_gemm_mixed(const Gemm& g, void* ws, int32_t* status, cudaStream_t s);
 size_t tc_gemm_ws_bytes(int M, int N, int K);
 // FP64 GEMM emulated on BF16 tensor cores with `slices` (6..8) base-128

@@ -8,6 +8,10 @@
 // BM x BN tile with DFMA from shared-memory stages of BK = 16, prefetching
 // the next stage into registers while the current one is consumed.
 #include <algorithm>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "common.cuh"
@@ -252,7 +256,32 @@ __global__ void gemv_finish(GemvDev g) {
   g.y[z][m] = v;
 }
 
+// ---- measured tile choice ---------------------------------------------------
+// A product's tile shape is timed once per (shape, layout, problems in the
+// launch) on scratch buffers and the fastest kept; untimed products use the
+// time model.  Timing runs only where a TuneScope is open (the eager first
+// evaluation before a graph is captured) and never inside stream capture.
+// The tile does not change a product's bits: every tile sums K in the same
+// order and the ranges it skips hold exact zeros.
+using TuneKey = std::tuple<int, int, int, int, int, int, int, int, int, int, int>;
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tuned;
+double* g_tscratch = nullptr;
+size_t g_tscratch_n = 0;
+thread_local int g_tune_depth = 0;
+
+bool autotune_on() {
+  static const bool v = [] {
+    const char* e = getenv("BTA_GEMM_AUTOTUNE");
+    return e ? atoi(e) != 0 : true;
+  }();
+  return v;
+}
+
 }  // namespace
+
+TuneScope::TuneScope() { ++g_tune_depth; }
+TuneScope::~TuneScope() { --g_tune_depth; }
 
 bta_status gemm_f64(const Gemm& g, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return BTA_OK;
@@ -325,38 +354,95 @@ bta_status gemm_f64(const Gemm& g, cudaStream_t s) {
     }
   }
   if (S > 1) bm = pick(nb * S);
-  GemmDev d;
-  d.M = g.M; d.N = g.N; d.K = K;
-  d.lda = g.lda; d.transA = g.transA; d.triA = g.triA;
-  d.ldb = g.ldb; d.transB = g.transB; d.triB = g.triB;
-  d.ldc = S > 1 ? g.M : g.ldc;
-  d.ldcin = S > 1 ? g.M : (g.Cin || g.Cinb ? g.ldcin : g.ldc);
-  d.alpha = S > 1 ? 1.0 : g.alpha;
-  d.beta = S > 1 ? 0.0 : g.beta;
-  d.out_lower = g.out_lower;
   const int np = (int)probs.size();
-  for (int z0 = 0; z0 < np; z0 += kMaxBatch) {
-    const int cnt = std::min(kMaxBatch, np - z0);
-    for (int z = 0; z < cnt; ++z) {
-      const Prob& q = probs[z0 + z];
-      d.A[z] = q.A; d.B[z] = q.B; d.C[z] = q.C; d.Cin[z] = q.Cin ? q.Cin : q.C;
-      d.kb[z] = q.kb; d.ke[z] = q.ke;
+  auto launch = [&](int tbm, const std::vector<Prob>& P) -> bta_status {
+    GemmDev d;
+    d.M = g.M; d.N = g.N; d.K = K;
+    d.lda = g.lda; d.transA = g.transA; d.triA = g.triA;
+    d.ldb = g.ldb; d.transB = g.transB; d.triB = g.triB;
+    d.ldc = S > 1 ? g.M : g.ldc;
+    d.ldcin = S > 1 ? g.M : (g.Cin || g.Cinb ? g.ldcin : g.ldc);
+    d.alpha = S > 1 ? 1.0 : g.alpha;
+    d.beta = S > 1 ? 0.0 : g.beta;
+    d.out_lower = g.out_lower;
+    for (int z0 = 0; z0 < np; z0 += kMaxBatch) {
+      const int cnt = std::min(kMaxBatch, np - z0);
+      for (int z = 0; z < cnt; ++z) {
+        const Prob& q = P[z0 + z];
+        d.A[z] = q.A; d.B[z] = q.B; d.C[z] = q.C; d.Cin[z] = q.Cin ? q.Cin : q.C;
+        d.kb[z] = q.kb; d.ke[z] = q.ke;
+      }
+      if (tbm == 0) {
+        dim3 grid(cdiv(g.M, 16), cdiv(g.N, 64), cnt);
+        launch_prio(gemm_f64_kernel<16, 64>, grid, dim3(NT), s, d);
+      } else if (tbm == 64) {
+        dim3 grid(cdiv(g.M, 64), cdiv(g.N, 64), cnt);
+        launch_prio(gemm_f64_kernel<64, 64>, grid, dim3(NT), s, d);
+      } else if (tbm == 32) {
+        dim3 grid(cdiv(g.M, 32), cdiv(g.N, 32), cnt);
+        launch_prio(gemm_f64_kernel<32, 32>, grid, dim3(NT), s, d);
+      } else {
+        dim3 grid(cdiv(g.M, 16), cdiv(g.N, 16), cnt);
+        launch_prio(gemm_f64_kernel<16, 16>, grid, dim3(NT), s, d);
+      }
+      BTA_LAUNCHED();
     }
-    if (bm == 0) {
-      dim3 grid(cdiv(g.M, 16), cdiv(g.N, 64), cnt);
-      launch_prio(gemm_f64_kernel<16, 64>, grid, dim3(NT), s, d);
-    } else if (bm == 64) {
-      dim3 grid(cdiv(g.M, 64), cdiv(g.N, 64), cnt);
-      launch_prio(gemm_f64_kernel<64, 64>, grid, dim3(NT), s, d);
-    } else if (bm == 32) {
-      dim3 grid(cdiv(g.M, 32), cdiv(g.N, 32), cnt);
-      launch_prio(gemm_f64_kernel<32, 32>, grid, dim3(NT), s, d);
-    } else {
-      dim3 grid(cdiv(g.M, 16), cdiv(g.N, 16), cnt);
-      launch_prio(gemm_f64_kernel<16, 16>, grid, dim3(NT), s, d);
+    return BTA_OK;
+  };
+  if (bm != 0 && autotune_on()) {
+    const TuneKey key{g.M, g.N, K, g.lda, g.ldb, g.transA, g.transB, g.triA, g.triB,
+                      g.out_lower, np};
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tuned.find(key);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (it == g_tuned.end() && g_tune_depth > 0 && cudaStreamIsCapturing(s, &cap) == cudaSuccess &&
+        cap == cudaStreamCaptureStatusNone) {
+      // scratch operands with the product's strides; every problem of the
+      // launch points at them (the scratch results are discarded)
+      const size_t fa = (size_t)g.lda * (g.transA ? g.M : std::max(K, 1));
+      const size_t fb = (size_t)g.ldb * (g.transB ? std::max(K, 1) : g.N);
+      const size_t fc = std::max((size_t)g.ldc * g.N, (size_t)g.M * g.N);
+      const size_t need = fa + fb + fc;
+      if (need > g_tscratch_n) {
+        if (g_tscratch) cudaFree(g_tscratch);
+        g_tscratch = nullptr;
+        g_tscratch_n = 0;
+        BTA_CUDA_TRY(cudaMalloc(&g_tscratch, need * sizeof(double)));
+        BTA_CUDA_TRY(cudaMemset(g_tscratch, 0, need * sizeof(double)));
+        g_tscratch_n = need;
+      }
+      std::vector<Prob> P(probs);
+      for (Prob& q : P) {
+        q.A = g_tscratch;
+        q.B = g_tscratch + fa;
+        q.C = g_tscratch + fa + fb;
+        q.Cin = q.Cin ? q.C : nullptr;
+      }
+      cudaEvent_t e0, e1;
+      BTA_CUDA_TRY(cudaEventCreate(&e0));
+      BTA_CUDA_TRY(cudaEventCreate(&e1));
+      int best = bm;
+      float best_ms = 1e30f;
+      for (int cand : {64, 32, 16}) {
+        float t = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+          BTA_CUDA_TRY(cudaEventRecord(e0, s));
+          BTA_TRY(launch(cand, P));
+          BTA_CUDA_TRY(cudaEventRecord(e1, s));
+          BTA_CUDA_TRY(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          BTA_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+          if (rep > 0) t = std::min(t, ms);   // the first run warms up
+        }
+        if (t < best_ms) { best_ms = t; best = cand; }
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      it = g_tuned.emplace(key, best).first;
     }
-    BTA_LAUNCHED();
+    if (it != g_tuned.end()) bm = it->second;
   }
+  BTA_TRY(launch(bm, probs));
   if (S > 1) {
     SplitDev r;
     r.M = g.M; r.N = g.N; r.S = S; r.ldc = g.ldc;
