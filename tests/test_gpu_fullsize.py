@@ -85,3 +85,49 @@ def test_large_ragged_model_fp64_and_mixed(P):
     assert _residual(prob, xm) < 1e-10
     np.testing.assert_allclose(pm["phase_c"], pc, rtol=1e-5, atol=1e-3)
     m.close()
+
+
+def test_production_model_emulated(P):
+    """Three coregionalised responses on a 40 x 40 grid, b = 4800, 192 time
+    blocks, a = 12, d = 15, 2e6 observations (141 GB of BTA blocks), in the
+    emulated-FP64 mode: log|Q_p| and all 15 Phase C terms against the spectral
+    closed form (the FP64 bar, 1e-10), and the two scaling identities of the
+    coregionalised prior (see test_oracle_pins), which tie the Phase A and
+    Phase B terms of every scale and coupling parameter to N and x*'Q_st x*."""
+    import time
+    from test_oracle_pins import _coreg_scaling_sums, _spectral_univariate
+    prob = workloads.make_problem("coreg_production")
+    assert prob.b == 4800 and prob.nt == 192 and prob.d == 15
+    m = P.InlaModel(prob)
+    t0 = time.perf_counter()
+    f, g = m.value_and_grad(prob.theta, use_graph=False, precision=2)
+    elapsed = time.perf_counter() - t0
+    parts = m.last_parts()
+    x = m.mode().cpu().numpy()
+    m.close()
+    print(f"production model, emulated FP64: {elapsed:.1f} s per f + gradient")
+    assert np.isfinite(f) and np.all(np.isfinite(g))
+    assert parts["fail_c"] < 0 and parts["fail_p"] < 0
+    k, th = prob.k, prob.theta
+    kap, gam, sig = np.exp(th[:k]), np.exp(th[k:2 * k]), np.exp(th[2 * k:3 * k])
+    nst = prob.nt * prob.ns
+    ld = -2.0 * nst * float(np.sum(np.log(sig))) + prob.a * np.log(1e-3)
+    pc = np.zeros(prob.d)
+    for v in range(k):
+        lam, dk, dg = _spectral_univariate(prob.nx, prob.ny, prob.nt, 1.0, kap[v], gam[v])
+        ld += float(np.sum(np.log(lam)))
+        pc[v] = 0.5 * np.sum(dk / lam)
+        pc[k + v] = 0.5 * np.sum(dg / lam)
+        pc[2 * k + v] = -nst
+    assert abs(parts["logdet_p"] - ld) <= 1e-10 * abs(ld)
+    np.testing.assert_allclose(parts["phase_c"], pc, rtol=1e-10, atol=1e-6)
+
+    class R:
+        phase_a, phase_b = parts["phase_a"], parts["phase_b"]
+    sa, sb = _coreg_scaling_sums(prob, R)
+    N = prob.N
+    # 0 <= 1e-3 tr(Z_T) <= a (the tip's Schur complement is at least 1e-3 I)
+    assert N - prob.a - 1e-9 * N <= sa <= N + 1e-9 * N
+    beta = x[N - prob.a:]
+    xqx = parts["quad"] - 1e-3 * float(beta @ beta)
+    assert abs(sb - xqx) <= 1e-10 * abs(xqx)

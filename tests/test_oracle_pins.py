@@ -243,3 +243,45 @@ def test_coregional_weights_definition():
         for q in range(k):
             blkpq = sum(W[m, pp, q] * mats[m] for m in range(k))
             np.testing.assert_allclose(big[pp * 4:(pp + 1) * 4, q * 4:(q + 1) * 4], blkpq, atol=1e-12)
+
+
+def _coreg_scaling_sums(p, res):
+    """The scaling identities of the coregionalised prior.  With
+    Lambda -> e^t Lambda (log sigma_m += t, lambda_pq *= e^t) the weights
+    (Lambda^-1)_mp (Lambda^-1)_mq, and so Q_st, scale by e^-2t:
+      sum_m A_{log sigma_m} + sum lambda_pq A_{lambda_pq} - 2 sum_m A_{log tau_m}
+          = N - 1e-3 tr(Z_T)
+      sum_m B_{log sigma_m} + sum lambda_pq B_{lambda_pq} = x*' Q_st x*
+    (A, B: the Phase A and Phase B terms; Z_T the tip block of Q_c^-1).
+    Returns the two left-hand sides."""
+    k = p.k
+    nc = k * (k - 1) // 2
+    th = p.theta
+    lam = th[3 * k:3 * k + nc]
+    pa, pb = np.asarray(res.phase_a), np.asarray(res.phase_b)
+    sa = (pa[2 * k:3 * k].sum() + float(lam @ pa[3 * k:3 * k + nc])
+          - 2.0 * pa[3 * k + nc:].sum())
+    sb = pb[2 * k:3 * k].sum() + float(lam @ pb[3 * k:3 * k + nc])
+    return sa, sb
+
+
+@pytest.mark.parametrize("name", ["coreg_tiny", "coreg_k2_small"])
+def test_multivariate_scaling_identities(name):
+    from oracle import dense
+    from oracle import model as M
+    p = workloads.make_problem(name)
+    res = bta.evaluate(p)
+    sa, sb = _coreg_scaling_sums(p, res)
+    mdl = M.build_model(p)
+    Z = np.linalg.inv(mdl.Qc.toarray())
+    N = Z.shape[0]
+    trzt = float(np.trace(Z[N - p.a:, N - p.a:]))
+    assert abs(sa - (N - 1e-3 * trzt)) <= 1e-9 * N
+    x = res.x
+    nst = N - p.a
+    xst = x[:nst]
+    assert abs(sb - float(xst @ (mdl.Qst @ xst))) <= 1e-9 * abs(sb)
+    # the same from the dense definition of every phase term
+    d = dense.evaluate(p)
+    sa2, sb2 = _coreg_scaling_sums(p, d)
+    assert abs(sa2 - sa) <= 1e-9 * N and abs(sb2 - sb) <= 1e-9 * abs(sb)
