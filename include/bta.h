@@ -96,6 +96,16 @@ typedef struct {
   const double* y;           /* n_obs */
   double tip_prior;          /* prior precision of each fixed effect (1e-3) */
   double theta_prior_var;    /* log p(theta) = -sum theta^2 / (2 var)  (100) */
+  int32_t low_memory;        /* 1: the model's evaluations keep only the diagonal
+                                factors L_Di^{-1} (and the arrow) between the
+                                forward and the reverse pass; every step that
+                                needs an off-diagonal factor re-assembles B_i
+                                and recomputes L_Bi = B_i L_Di^{-T} (the
+                                carry-based variant of Algorithm 1, Section
+                                III-A): about half the device memory, one more
+                                b x b product per block.  Precision 1 (mixed)
+                                is refused (BTA_ERR_ARG) on such a model.  0:
+                                both factors kept whole.                       */
 } inla_model_spec;
 
 typedef struct inla_model inla_model;

@@ -39,7 +39,8 @@ class inla_model_spec(C.Structure):
                 ("n_obs", C.c_int64),
                 ("obs_t", C.c_void_p), ("obs_s", C.c_void_p), ("obs_v", C.c_void_p),
                 ("obs_cov", C.c_void_p), ("y", C.c_void_p),
-                ("tip_prior", C.c_double), ("theta_prior_var", C.c_double)]
+                ("tip_prior", C.c_double), ("theta_prior_var", C.c_double),
+                ("low_memory", C.c_int32)]
 
 
 class inla_opts(C.Structure):

@@ -59,7 +59,8 @@ def _temporal(nt: int):
 class InlaModel:
     """A model on the current CUDA device (inla_model_create)."""
 
-    def __init__(self, prob, tip_prior: float = 1e-3, theta_prior_var: float = 100.0):
+    def __init__(self, prob, tip_prior: float = 1e-3, theta_prior_var: float = 100.0,
+                 low_memory: bool = False):
         L = lib()
         self.prob = prob
         row_ptr, col, vC, vG, vGG = grid_stencil(prob.nx, prob.ny)
@@ -76,7 +77,8 @@ class InlaModel:
             row_ptr=_ptr(row_ptr), col=_ptr(col), val_C=_ptr(vC), val_G=_ptr(vG),
             val_GG=_ptr(vGG), m_diag=_ptr(mdiag), m_sub=_ptr(msub), n_obs=int(y.shape[0]),
             obs_t=_ptr(obs_t), obs_s=_ptr(obs_s), obs_v=_ptr(obs_v), obs_cov=_ptr(cov),
-            y=_ptr(y), tip_prior=tip_prior, theta_prior_var=theta_prior_var)
+            y=_ptr(y), tip_prior=tip_prior, theta_prior_var=theta_prior_var,
+            low_memory=int(bool(low_memory)))
         h = C.c_void_p()
         torch.cuda.init()
         check(L.inla_model_create(C.byref(spec), C.byref(h)), "inla_model_create")

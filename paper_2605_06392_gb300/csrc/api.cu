@@ -37,6 +37,7 @@ struct EvalCtx {
   SweepWs wsc, wsp;
   SelinvFuse fc, fp;
   double* dr = nullptr;         // mixed mode: refinement residual / correction
+  double *w4c = nullptr, *w4p = nullptr;   // low memory: second L_B buffer per sweep
   int have_factors = 0;         // last evaluation was value-only: factors still held
 };
 
@@ -51,6 +52,7 @@ struct inla_model {
   CoefLayout L;
   int n = 0, b = 0, ld = 0, a = 0, d = 0;
   int nslots = 0;
+  int lowmem = 0;               // keep only the diagonal factors (see inla_model_spec)
   std::vector<EvalCtx> ctx;     // grown on demand (batched evaluations)
   std::vector<void*> allocs;
   // host
@@ -111,13 +113,19 @@ bta_status ctx_alloc(inla_model* m, EvalCtx& c) {
   BTA_TRY(dmalloc(m, &c.coefbuf, m->L.total));
   c.qc.n = nt; c.qc.b = md.b; c.qc.a = a; c.qc.ld = ld;
   BTA_TRY(dmalloc(m, &c.qc.D, nt * blk));
-  BTA_TRY(dmalloc(m, &c.qc.B, std::max(nt - 1, 1) * blk));
+  if (!m->lowmem) BTA_TRY(dmalloc(m, &c.qc.B, std::max(nt - 1, 1) * blk));
   BTA_TRY(dmalloc(m, &c.qc.C, std::max<size_t>((size_t)nt * a * ld, 1)));
   BTA_TRY(dmalloc(m, &c.qc.T, std::max(a * a, 1)));
   c.qp = c.qc;
   c.qp.a = 0; c.qp.C = nullptr; c.qp.T = nullptr;
   BTA_TRY(dmalloc(m, &c.qp.D, nt * blk));
-  BTA_TRY(dmalloc(m, &c.qp.B, std::max(nt - 1, 1) * blk));
+  if (!m->lowmem) {
+    BTA_TRY(dmalloc(m, &c.qp.B, std::max(nt - 1, 1) * blk));
+  } else {
+    c.qp.B = nullptr;
+    BTA_TRY(dmalloc(m, &c.w4c, blk));
+    BTA_TRY(dmalloc(m, &c.w4p, blk));
+  }
   BTA_TRY(dmalloc(m, &c.x, (size_t)nt * ld + a));
   BTA_TRY(dmalloc(m, &c.slots_c, m->nslots));
   BTA_TRY(dmalloc(m, &c.slots_p, m->nslots));
@@ -187,6 +195,11 @@ bta_status record_group(inla_model* m, int mode, int cnt, int prec, cudaStream_t
     ic[e].ws = c.wsc; ic[e].fuse = &c.fc;
     ip[e].q = c.qp; ip[e].vec = nullptr; ip[e].slots = c.slots_p; ip[e].fail = c.fail + 1;
     ip[e].ws = c.wsp; ip[e].fuse = &c.fp;
+    ic[e].md = ip[e].md = &md;
+    ic[e].lay = ip[e].lay = &m->L;
+    ic[e].coef = ip[e].coef = c.coefbuf;
+    ic[e].W4 = c.w4c;
+    ip[e].W4 = c.w4p;
   }
   if (mode < 2) {
     for (int e = 0; e < cnt; ++e) {
@@ -355,6 +368,7 @@ void inla_model_destroy(inla_model* m) {
 
 static bta_status model_create_impl(const inla_model_spec* sp, inla_model* m) {
   ModelDev& md = m->md;
+  m->lowmem = sp->low_memory != 0;
   const int k = sp->k, ns = sp->ns, nt = sp->nt, a = sp->a;
   if (k < 1 || k > kMaxK || ns < 1 || nt < 1 || a < 0 || a % k || a > 32 || sp->nnz < 1 ||
       !sp->row_ptr || !sp->col || !sp->val_C || !sp->val_G || !sp->val_GG || !sp->m_diag ||
@@ -609,6 +623,7 @@ bta_status inla_value_and_grad(inla_model* m, const double* theta, int32_t batch
   if (!m || !theta || !f || batch < 1) return BTA_ERR_ARG;
   const int prec = opts ? opts->precision : 0;
   if (prec < 0 || prec > 2) return BTA_ERR_ARG;
+  if (prec == 1 && m->lowmem) return BTA_ERR_ARG;   // its refinement solves read the B blocks
   for (int i = 0; i < batch; ++i)
     if (!finite_theta(theta + (size_t)i * m->d, m->d)) return BTA_ERR_ARG;
   const int use_graph = opts ? opts->use_graph : 1;
@@ -743,6 +758,8 @@ bta_status inla_batch_value_and_grad(inla_batch* b, const double* theta, int32_t
   if (prec < 0 || prec > 2) return BTA_ERR_ARG;
   const int g = grad ? 1 : 0;
   const int nm = (int)b->models.size();
+  for (int i = 0; i < nm; ++i)   // mixed mode's refinement solves read the B blocks
+    if (prec == 1 && b->models[i]->lowmem) return BTA_ERR_ARG;
   for (int i = 0; i < nm; ++i) {
     inla_model* m = b->models[i];
     if (m->d > ldt || !finite_theta(theta + (size_t)i * ldt, m->d)) return BTA_ERR_ARG;

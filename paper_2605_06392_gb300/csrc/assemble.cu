@@ -143,6 +143,7 @@ __global__ void coef_kernel(CoefArgs a, double* buf) {
 
 struct AsmArgs {
   int k, ns, b, ld, nnz, cond, diag;
+  int t0;                 // time block of output block 0 (coefficients, counts)
   const int32_t* row_ptr;
   const int32_t* col;
   const double* val;      // [kNS][nnz]
@@ -151,11 +152,12 @@ struct AsmArgs {
   const double* cnt;      // [nt*ld]
 };
 
-// One CTA per column c of block t: zero-fill, then scatter the stencil.
+// One CTA per column c of output block blockIdx.y (time block t0 + blockIdx.y):
+// zero-fill, then scatter the stencil.
 __global__ void __launch_bounds__(256) assemble_kernel(AsmArgs a, double* out) {
-  const int c = blockIdx.x, t = blockIdx.y;
+  const int c = blockIdx.x, t = a.t0 + blockIdx.y;
   const int ld = a.ld;
-  double* colp = out + ((int64_t)t * ld + c) * ld;
+  double* colp = out + ((int64_t)blockIdx.y * ld + c) * ld;
   double2* col2 = reinterpret_cast<double2*>(colp);
   for (int r = threadIdx.x; r < ld / 2; r += blockDim.x) col2[r] = make_double2(0.0, 0.0);
   __syncthreads();
@@ -234,11 +236,11 @@ bta_status launch_rhs(const ModelDev& md, const CoefLayout& L, const double* coe
 bta_status launch_assemble(const ModelDev& md, const CoefLayout& L, const double* coefbuf,
                            int cond, const bta_desc& q, double* rhs, cudaStream_t s) {
   const int ld = md.ld;
-  AsmArgs a{md.k, md.ns, md.b, ld, md.nnz, cond, 1, md.row_ptr, md.col, md.val,
+  AsmArgs a{md.k, md.ns, md.b, ld, md.nnz, cond, 1, 0, md.row_ptr, md.col, md.val,
             coefbuf + L.alphaD, coefbuf + L.tau, md.cnt};
   assemble_kernel<<<dim3(ld, md.nt), 256, 0, s>>>(a, q.D);
   BTA_LAUNCHED();
-  if (md.nt > 1) {
+  if (md.nt > 1 && q.B) {   // no B storage: the sweeps assemble B_i per step
     a.diag = 0;
     a.alpha = coefbuf + L.alphaB;
     assemble_kernel<<<dim3(ld, md.nt - 1), 256, 0, s>>>(a, q.B);
@@ -259,6 +261,16 @@ bta_status launch_assemble(const ModelDev& md, const CoefLayout& L, const double
                                                  coefbuf + L.tau, md.rraw, rhs);
     BTA_LAUNCHED();
   }
+  return BTA_OK;
+}
+
+bta_status launch_assemble_b(const ModelDev& md, const CoefLayout& L, const double* coefbuf,
+                             int i, double* dst, cudaStream_t s) {
+  if (i < 0 || i >= md.nt - 1) return BTA_ERR_ARG;
+  AsmArgs a{md.k, md.ns, md.b, md.ld, md.nnz, 0, 0, i, md.row_ptr, md.col, md.val,
+            coefbuf + L.alphaB, coefbuf + L.tau, md.cnt};
+  assemble_kernel<<<dim3(md.ld, 1), 256, 0, s>>>(a, dst);
+  BTA_LAUNCHED();
   return BTA_OK;
 }
 

@@ -60,6 +60,11 @@ bta_status launch_coef(const ModelDev& md, const CoefLayout& L, double* coefbuf,
 bta_status launch_assemble(const ModelDev& md, const CoefLayout& L, const double* coefbuf,
                            int cond, const bta_desc& q, double* rhs, cudaStream_t s);
 
+// The one off-diagonal block B_i (= Q[i+1, i]) of Q_p, which Q_c shares, into
+// dst (ld x ld); for sweeps that do not keep the B blocks.
+bta_status launch_assemble_b(const ModelDev& md, const CoefLayout& L, const double* coefbuf,
+                             int i, double* dst, cudaStream_t s);
+
 // --- reduce.cu --------------------------------------------------------------
 // Sizes of the per-block partial-sum arrays.
 int pattern_chunks(const ModelDev& md);

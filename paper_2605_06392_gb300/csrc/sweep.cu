@@ -179,7 +179,10 @@ bta_status sum_slots(const double* parts, int nparts, double* out, int accumulat
 
 size_t SweepWs::bytes(int ld, int a) {
   size_t m = (size_t)ld * ld;
-  return sizeof(double) * (4 * m + 2 * (size_t)a * ld + (size_t)kGemvSplit * ld + a + 64);
+  // a multiple of 256 bytes: a second workspace carved right after this one
+  // keeps its blocks aligned for vector access
+  const size_t d = 4 * m + 2 * (size_t)a * ld + (size_t)kGemvSplit * ld + a + 64;
+  return sizeof(double) * ((d + 31) / 32 * 32);
 }
 
 void SweepWs::carve(double* base, int ld, int a) {
@@ -260,10 +263,22 @@ bta_status big_product(const Gemm& g, const SweepItem* it, const std::vector<int
 
 bta_status check_set(const SweepItem* it, int m) {
   if (m < 1) return BTA_ERR_ARG;
+  const bool low = it[0].q.B == nullptr;
   for (int z = 0; z < m; ++z) {
     if (it[z].q.n != it[0].q.n || it[z].q.ld != it[0].q.ld) return BTA_ERR_ARG;
     if (it[z].q.a > kMaxTip) return BTA_ERR_ARG;
+    if ((it[z].q.B == nullptr) != low) return BTA_ERR_ARG;
+    if (low && it[z].q.n > 1 && (!it[z].md || !it[z].lay || !it[z].coef || !it[z].W4))
+      return BTA_ERR_ARG;
   }
+  return BTA_OK;
+}
+
+// Low-memory sweeps: B_i of every item of idx into the item's W2.
+bta_status assemble_b_items(const SweepItem* it, const std::vector<int>& idx, int i,
+                            cudaStream_t s) {
+  for (int z : idx)
+    BTA_TRY(launch_assemble_b(*it[z].md, *it[z].lay, it[z].coef, i, it[z].ws.W2, s));
   return BTA_OK;
 }
 
@@ -287,10 +302,15 @@ bta_status factor_sweep_multi(const SweepItem* it, int m, cudaStream_t s, cudaEv
   auto D = [&](int z, int i) { return it[z].q.D + i * blk; };
   auto B = [&](int z, int i) { return it[z].q.B + i * blk; };
   auto Cb = [&](int z, int i) { return it[z].q.C + (int64_t)i * it[z].q.a * ld; };
+  const bool low = it[0].q.B == nullptr;
+  // where L_Bi lives: in place of B_i, or (low memory) in W1 / W4 by parity
+  auto LB = [&](int z, int i) {
+    return low ? ((i & 1) ? it[z].W4 : it[z].ws.W1) : B(z, i);
+  };
   for (int i = 0; i < n; ++i) {
     if (i > 0) {
       {  // D_i -= S_{i-1} = L_B,i-1 L_B,i-1^T (lower)
-        auto Bp = ptrs(G.all, [&](int z) { return B(z, i - 1); });
+        auto Bp = ptrs(G.all, [&](int z) { return LB(z, i - 1); });
         auto Di = ptrs(G.all, [&](int z) { return D(z, i); });
         Gemm g; g.M = ld; g.N = ld; g.K = ld; g.batch = M;
         g.Ab = cp(Bp); g.lda = ld; g.Bb = cp(Bp); g.ldb = ld; g.transB = 1;
@@ -301,7 +321,7 @@ bta_status factor_sweep_multi(const SweepItem* it, int m, cudaStream_t s, cudaEv
       for (const auto& grp : G.arrow) {  // C_i -= L_C,i-1 L_B,i-1^T
         const int a = it[grp[0]].q.a;
         auto Cp = ptrs(grp, [&](int z) { return Cb(z, i - 1); });
-        auto Bp = ptrs(grp, [&](int z) { return B(z, i - 1); });
+        auto Bp = ptrs(grp, [&](int z) { return LB(z, i - 1); });
         auto Ci = ptrs(grp, [&](int z) { return Cb(z, i); });
         auto SK = ptrs(grp, [&](int z) { return it[z].ws.W3; });   // W3 is free here
         Gemm g; g.M = a; g.N = ld; g.K = ld; g.batch = (int)grp.size();
@@ -342,21 +362,22 @@ bta_status factor_sweep_multi(const SweepItem* it, int m, cudaStream_t s, cudaEv
       BTA_TRY(gemm_f64(h, s));
     }
     if (i < n - 1) {  // L_Bi = B_i L_Di^{-T}
-      auto Bi = ptrs(G.all, [&](int z) { return B(z, i); });
+      if (low) BTA_TRY(assemble_b_items(it, G.all, i, s));
+      auto Bi = ptrs(G.all, [&](int z) { return low ? it[z].ws.W2 : B(z, i); });
       auto Di = ptrs(G.all, [&](int z) { return D(z, i); });
-      auto W = ptrs(G.all, [&](int z) { return it[z].ws.W1; });
+      auto W = ptrs(G.all, [&](int z) { return low ? LB(z, i) : it[z].ws.W1; });
       Gemm g; g.M = ld; g.N = ld; g.K = ld; g.batch = M;
       g.Ab = cp(Bi); g.lda = ld; g.Bb = cp(Di); g.ldb = ld; g.transB = 1; g.triB = TRI_UPPER;
       g.Cb = W.data(); g.ldc = ld;
       BTA_TRY(big_product(g, it, G.all, precision, s));
-      BTA_TRY(copy_block_batch(M, cp(W), ld, Bi.data(), ld, ld, ld, 1.0, 0, s));
+      if (!low) BTA_TRY(copy_block_batch(M, cp(W), ld, Bi.data(), ld, ld, ld, 1.0, 0, s));
     }
     if (!G.vec.empty()) {  // z_i = L_Di^{-1} (r_i - L_B,i-1 z_{i-1});  v_T += L_Ci z_i
       const int c = (int)G.vec.size();
       auto ri = ptrs(G.vec, [&](int z) { return it[z].vec + (int64_t)i * ld; });
       auto gv = ptrs(G.vec, [&](int z) { return it[z].ws.gv; });
       if (i > 0) {
-        auto Bp = ptrs(G.vec, [&](int z) { return B(z, i - 1); });
+        auto Bp = ptrs(G.vec, [&](int z) { return LB(z, i - 1); });
         auto rp = ptrs(G.vec, [&](int z) { return it[z].vec + (int64_t)(i - 1) * ld; });
         Gemv g; g.M = ld; g.K = ld; g.lda = ld; g.alpha = -1.0; g.beta = 1.0; g.batch = c;
         g.Ab = cp(Bp); g.xb = cp(rp); g.yb = ri.data(); g.yinb = cp(ri); g.workb = gv.data();
@@ -465,13 +486,28 @@ bta_status upper_solve_multi(const SweepItem* it, int m, cudaStream_t s) {
       g.x = it[z].vec + (int64_t)n * ld; g.y = zz; g.yin = zz; g.alpha = -1.0; g.beta = 1.0;
       BTA_TRY(gemv_f64(g, it[z].ws.gv, s));
     }
-    if (i < n - 1) {  // z_i -= L_Bi^T x_{i+1}
+    if (i < n - 1 && it[0].q.B) {  // z_i -= L_Bi^T x_{i+1}
       auto Bi = ptrs(G.vec, [&](int z) { return it[z].q.B + i * blk; });
       auto xn = ptrs(G.vec, [&](int z) { return it[z].vec + (int64_t)(i + 1) * ld; });
       Gemv g; g.M = ld; g.K = ld; g.lda = ld; g.transA = 1; g.alpha = -1.0; g.beta = 1.0;
       g.batch = c; g.Ab = cp(Bi); g.xb = cp(xn); g.yb = zi.data(); g.yinb = cp(zi);
       g.workb = gv.data();
       BTA_TRY(gemv_f64(g, nullptr, s));
+    } else if (i < n - 1) {
+      // low memory: L_Bi^T x_{i+1} = L_Di^{-1} (B_i^T x_{i+1}), B_i assembled into W2,
+      // the product into W3's first ld entries
+      BTA_TRY(assemble_b_items(it, G.vec, i, s));
+      auto W2 = ptrs(G.vec, [&](int z) { return it[z].ws.W2; });
+      auto t = ptrs(G.vec, [&](int z) { return it[z].ws.W3; });
+      auto xn = ptrs(G.vec, [&](int z) { return it[z].vec + (int64_t)(i + 1) * ld; });
+      Gemv g; g.M = ld; g.K = ld; g.lda = ld; g.transA = 1; g.batch = c;
+      g.Ab = cp(W2); g.xb = cp(xn); g.yb = t.data(); g.workb = gv.data();
+      BTA_TRY(gemv_f64(g, nullptr, s));
+      auto Di = ptrs(G.vec, [&](int z) { return it[z].q.D + i * blk; });
+      Gemv h; h.M = ld; h.K = ld; h.lda = ld; h.triA = TRI_LOWER; h.alpha = -1.0; h.beta = 1.0;
+      h.batch = c; h.Ab = cp(Di); h.xb = cp(t); h.yb = zi.data(); h.yinb = cp(zi);
+      h.workb = gv.data();
+      BTA_TRY(gemv_f64(h, nullptr, s));
     }
     {  // x_i = L_Di^{-T} z_i
       auto Di = ptrs(G.vec, [&](int z) { return it[z].q.D + i * blk; });
@@ -513,11 +549,19 @@ bta_status selinv_sweep_multi(const SweepItem* it, int m, cudaStream_t s, int pr
   auto W1 = ptrs(G.all, [&](int z) { return it[z].ws.W1; });
   auto W2 = ptrs(G.all, [&](int z) { return it[z].ws.W2; });
   auto W3 = ptrs(G.all, [&](int z) { return it[z].ws.W3; });
+  const bool low = it[0].q.B == nullptr;
   for (int i = n - 1; i >= 0; --i) {
     const bool hasB = i < n - 1;
     auto Di = ptrs(G.all, [&](int z) { return D(z, i); });
+    if (hasB && low) {  // low memory: W3 = L_Bi = B_i L_Di^{-T}, B_i assembled into W2
+      BTA_TRY(assemble_b_items(it, G.all, i, s));
+      Gemm g; g.M = ld; g.N = ld; g.K = ld; g.batch = M;
+      g.Ab = cp(W2); g.lda = ld; g.Bb = cp(Di); g.ldb = ld; g.transB = 1; g.triB = TRI_UPPER;
+      g.Cb = W3.data(); g.ldc = ld;
+      BTA_TRY(big_product(g, it, G.all, precision, s));
+    }
     if (hasB) {  // W1 = F_B = L_Bi L_Di^{-1}
-      auto Bi = ptrs(G.all, [&](int z) { return B(z, i); });
+      auto Bi = ptrs(G.all, [&](int z) { return low ? it[z].ws.W3 : B(z, i); });
       Gemm g; g.M = ld; g.N = ld; g.K = ld; g.batch = M;
       g.Ab = cp(Bi); g.lda = ld; g.Bb = cp(Di); g.ldb = ld; g.triB = TRI_LOWER;
       g.Cb = W1.data(); g.ldc = ld;
@@ -601,7 +645,7 @@ bta_status selinv_sweep_multi(const SweepItem* it, int m, cudaStream_t s, int pr
       BTA_TRY(gemm_f64(g, s));
     }
     BTA_TRY(copy_block_batch(M, cp(W3), ld, Di.data(), ld, ld, ld, 1.0, 1, s));   // Z_D (full)
-    if (hasB) {
+    if (hasB && !low) {   // Z_B in place of L_Bi (low memory: reduced from W2 below)
       auto Bi = ptrs(G.all, [&](int z) { return B(z, i); });
       BTA_TRY(copy_block_batch(M, cp(W2), ld, Bi.data(), ld, ld, ld, 1.0, 0, s));
     }
@@ -619,7 +663,8 @@ bta_status selinv_sweep_multi(const SweepItem* it, int m, cudaStream_t s, int pr
       BTA_TRY(launch_pattern_dot(md, D(z, i), fz->counts, i,
                                  fz->PD + (int64_t)i * kk * pch * kNP, s));
       if (hasB)
-        BTA_TRY(launch_pattern_dot(md, B(z, i), 0, i, fz->PB + (int64_t)i * kk * pch * kNP, s));
+        BTA_TRY(launch_pattern_dot(md, low ? it[z].ws.W2 : B(z, i), 0, i,
+                                   fz->PB + (int64_t)i * kk * pch * kNP, s));
       if (it[z].q.a > 0 && fz->PC)
         BTA_TRY(launch_arrow_dot(md, Cb(z, i), i, fz->PC + (int64_t)i * md.k * arrow_chunks(md),
                                  s));

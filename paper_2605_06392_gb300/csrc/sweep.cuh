@@ -39,6 +39,14 @@ struct SweepItem {
   int32_t* fail = nullptr;         // factor: failure flag (first failing block)
   SweepWs ws;
   const SelinvFuse* fuse = nullptr;   // selected inversion: fused Eq. 7 sums (or null)
+  // Low-memory sweeps (q.B == nullptr): the off-diagonal factors L_Bi are not
+  // kept; B_i is assembled from the model when a step needs it and L_Bi =
+  // B_i L_Di^{-T} recomputed.  W4 (ld x ld) holds every other L_Bi of the
+  // factor sweep.
+  const ModelDev* md = nullptr;
+  const CoefLayout* lay = nullptr;
+  const double* coef = nullptr;
+  double* W4 = nullptr;
 };
 // mark (optional): recorded on s right after block 0's diagonal factor, so a
 // concurrent sweep can start one diagonal step behind this one.

@@ -9,6 +9,8 @@ times (inla_value_and_grad, CUDA graph, two sweep streams).
 * 45x45 grid, b = 2025 (ld = 2048, a ragged tail), 100 time blocks: the
   closed forms and the residual, and the mixed-precision mode against the
   FP64 path (1e-6 on f, 1e-4 per gradient component).
+* 3 x 40x40 grid, b = 4800, 192 time blocks, d = 15 (the production model),
+  emulated FP64 with the low-memory sweeps: closed forms and identities.
 """
 import numpy as np
 import pytest
@@ -87,25 +89,33 @@ def test_large_ragged_model_fp64_and_mixed(P):
     m.close()
 
 
-def test_production_model_emulated(P):
+def test_production_model_emulated_low_memory(P):
     """Three coregionalised responses on a 40 x 40 grid, b = 4800, 192 time
-    blocks, a = 12, d = 15, 2e6 observations (141 GB of BTA blocks), in the
-    emulated-FP64 mode: log|Q_p| and all 15 Phase C terms against the spectral
+    blocks, a = 12, d = 15, 2e6 observations, in the emulated-FP64 mode with
+    the low-memory sweeps (only the diagonal factors kept: ~71 GB of blocks
+    instead of 141 GB): log|Q_p| and all 15 Phase C terms against the spectral
     closed form (the FP64 bar, 1e-10), and the two scaling identities of the
     coregionalised prior (see test_oracle_pins), which tie the Phase A and
     Phase B terms of every scale and coupling parameter to N and x*'Q_st x*."""
     import time
+    import torch
     from test_oracle_pins import _coreg_scaling_sums, _spectral_univariate
     prob = workloads.make_problem("coreg_production")
     assert prob.b == 4800 and prob.nt == 192 and prob.d == 15
-    m = P.InlaModel(prob)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    m = P.InlaModel(prob, low_memory=True)
     t0 = time.perf_counter()
     f, g = m.value_and_grad(prob.theta, use_graph=False, precision=2)
     elapsed = time.perf_counter() - t0
+    free1, _ = torch.cuda.mem_get_info()
     parts = m.last_parts()
     x = m.mode().cpu().numpy()
     m.close()
-    print(f"production model, emulated FP64: {elapsed:.1f} s per f + gradient")
+    used = (free0 - free1) / 2 ** 30
+    print(f"production model, emulated FP64, low memory: {elapsed:.1f} s per f + gradient, "
+          f"{used:.1f} GiB on the device")
+    assert used < 90.0   # both factors kept whole would take > 131 GiB
     assert np.isfinite(f) and np.all(np.isfinite(g))
     assert parts["fail_c"] < 0 and parts["fail_p"] < 0
     k, th = prob.k, prob.theta
