@@ -160,116 +160,159 @@ struct FinArgs {
   Reductions r;
 };
 
-__global__ void __launch_bounds__(RT) finalize_kernel(FinArgs a, const double* coefbuf,
-                                                      double* out) {
+// Sum over a warp (every lane gets the total).
+__device__ __forceinline__ double warp_total(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+constexpr int kFinThreads = 1024;
+
+// The combination of Eq. 1 and Eq. 6 from the per-block partial sums.  On
+// GB300 every dependent FP64 add costs ~64 cycles, so each sum is split over
+// the lanes of a warp (fixed order: the result is deterministic) and the
+// warps take different sums.
+__global__ void __launch_bounds__(kFinThreads) finalize_kernel(FinArgs a, const double* coefbuf,
+                                                               double* out) {
   // R[j][pq][s] sums for Q_c (RDc), Q_p (RDp) and the mode's quadratic form (RX).
   __shared__ double RDc[kNJ][kMaxK * kMaxK][kNS], RDp[kNJ][kMaxK * kMaxK][kNS],
       RX[kNJ][kMaxK * kMaxK][kNS];
-  __shared__ double CNT[kMaxK], PC[kMaxK], TT[kMaxK], RS[kMaxK];
-  const int tid = threadIdx.x, kk = a.kk, nt = a.nt, pch = a.pch;
+  __shared__ double CNT[kMaxK], PC[kMaxK], TT[kMaxK], RS[kMaxK], SL[2];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int kk = a.kk, nt = a.nt, pch = a.pch, k = a.k;
   const Reductions& r = a.r;
-  // thread -> (which of 3 arrays, pq, s)
-  for (int w = tid; w < 3 * kk * kNS; w += blockDim.x) {
-    int which = w / (kk * kNS), pq = (w / kNS) % kk, s = w % kNS;
+  // (1) pattern sums: one warp per (array, pq, s), lanes over (block, chunk)
+  for (int w = warp; w < 3 * kk * kNS; w += nw) {
+    const int which = w / (kk * kNS), pq = (w / kNS) % kk, s = w % kNS;
     const double* PD = which == 0 ? r.PDc : which == 1 ? r.PDp : r.QD;
     const double* PB = which == 0 ? r.PBc : which == 1 ? r.PBp : r.QB;
     double acc[kNJ] = {0.0, 0.0, 0.0};
     if (which == 2 || a.grad) {
-      for (int t = 0; t < nt; ++t) {
-        double sd = 0.0;
-        const double* pd = PD + (((int64_t)t * kk + pq) * pch) * kNP + s;
-        for (int c = 0; c < pch; ++c) sd += pd[c * kNP];
-        for (int j = 0; j < kNJ; ++j) acc[j] = fma(a.m_diag[j * nt + t], sd, acc[j]);
-        if (t + 1 < nt) {
-          double sb = 0.0;
-          const double* pb = PB + (((int64_t)t * kk + pq) * pch) * kNP + s;
-          for (int c = 0; c < pch; ++c) sb += pb[c * kNP];
-          for (int j = 0; j < kNJ; ++j)
-            acc[j] = fma(2.0 * a.m_sub[j * (nt - 1) + t], sb, acc[j]);
+      const int nd = nt * pch, nb = (nt - 1) * pch;
+      for (int u = lane; u < nd + nb; u += 32) {
+        const bool isb = u >= nd;
+        const int uu = isb ? u - nd : u, t = uu / pch, c = uu % pch;
+        const double v = (isb ? PB : PD)[(((int64_t)t * kk + pq) * pch + c) * kNP + s];
+#pragma unroll
+        for (int j = 0; j < kNJ; ++j) {
+          const double m = isb ? 2.0 * a.m_sub[j * (nt - 1) + t] : a.m_diag[j * nt + t];
+          acc[j] = fma(m, v, acc[j]);
         }
       }
+#pragma unroll
+      for (int j = 0; j < kNJ; ++j) acc[j] = warp_total(acc[j]);
     }
-    for (int j = 0; j < kNJ; ++j) {
-      if (which == 0) RDc[j][pq][s] = acc[j];
-      else if (which == 1) RDp[j][pq][s] = acc[j];
-      else RX[j][pq][s] = acc[j];
-    }
+    if (lane == 0)
+      for (int j = 0; j < kNJ; ++j) {
+        if (which == 0) RDc[j][pq][s] = acc[j];
+        else if (which == 1) RDp[j][pq][s] = acc[j];
+        else RX[j][pq][s] = acc[j];
+      }
   }
-  if (tid < a.k) {
-    int m = tid;
-    double cnt = 0.0, pc = 0.0, tt = 0.0, rs = 0.0;
-    if (a.grad) {
-      int mm = m * a.k + m;
-      for (int t = 0; t < nt; ++t) {
-        const double* pd = r.PDc + (((int64_t)t * kk + mm) * pch) * kNP + 3;
-        for (int c = 0; c < pch; ++c) cnt += pd[c * kNP];
-        if (a.a > 0) {
-          const double* pcp = r.PCc + ((int64_t)t * a.k + m) * a.ach;
-          for (int c = 0; c < a.ach; ++c) pc += pcp[c];
+  // (2) per response: counts, arrow and tip traces, residual sums; the two
+  // log-determinant slot sums
+  for (int w = warp; w < 4 * k + 2; w += nw) {
+    double v = 0.0;
+    if (w < 4 * k) {
+      const int q = w / k, m = w % k;
+      if (q == 0 && a.grad) {          // sum of the count-diagonal pattern term
+        const int mm = m * k + m;
+        for (int u = lane; u < nt * pch; u += 32) {
+          const int t = u / pch, c = u % pch;
+          v += r.PDc[(((int64_t)t * kk + mm) * pch + c) * kNP + 3];
         }
-      }
-      if (a.a > 0) {
+      } else if (q == 1 && a.grad && a.a > 0) {
+        for (int u = lane; u < nt * a.ach; u += 32) {
+          const int t = u / a.ach, c = u % a.ach;
+          v += r.PCc[((int64_t)t * k + m) * a.ach + c];
+        }
+      } else if (q == 2 && a.grad && a.a > 0) {
         const double* tr = a.traw + (int64_t)m * a.a * a.a;
-        for (int i = 0; i < a.a * a.a; ++i) tt += r.ZTc[i] * tr[i];
+        for (int i = lane; i < a.a * a.a; i += 32) v = fma(r.ZTc[i], tr[i], v);
+      } else if (q == 3) {
+        for (int c = lane; c < a.rch; c += 32) v += r.RS[(int64_t)m * a.rch + c];
       }
+      v = warp_total(v);
+      if (lane == 0) {
+        if (q == 0) CNT[m] = v;
+        else if (q == 1) PC[m] = v;
+        else if (q == 2) TT[m] = v;
+        else RS[m] = v;
+      }
+    } else {
+      const bool cond = w == 4 * k;
+      const double* sl = cond ? r.ldc : r.ldp;
+      const int ns = cond ? a.nldc : a.nldp;
+      for (int i = lane; i < ns; i += 32) v += sl[i];
+      v = warp_total(v);
+      if (lane == 0) SL[cond ? 0 : 1] = v;
     }
-    for (int c = 0; c < a.rch; ++c) rs += r.RS[(int64_t)m * a.rch + c];
-    CNT[m] = cnt; PC[m] = pc; TT[m] = tt; RS[m] = rs;
   }
   __syncthreads();
-  if (tid != 0) return;
   const CoefLayout& L = a.L;
   const double* th = coefbuf + L.theta;
   const double* tau = coefbuf + L.tau;
   const double* coef = coefbuf + L.coef;
   const double* dcoef = coefbuf + L.dcoef;
-  const int d = a.d, k = a.k;
-  double ldc = 0.0, ldp = 0.0;
-  for (int i = 0; i < a.nldc; ++i) ldc += r.ldc[i];
-  for (int i = 0; i < a.nldp; ++i) ldp += r.ldp[i];
-  ldp += a.a * log(a.tip);
-  double quad = 0.0;
-  for (int pq = 0; pq < kk; ++pq)
-    for (int j = 0; j < kNJ; ++j)
-      for (int s = 0; s < kNS; ++s) quad += coef[(pq * kNJ + j) * kNS + s] * RX[j][pq][s];
-  const double* beta = r.x + (int64_t)nt * a.ld;
-  for (int i = 0; i < a.a; ++i) quad += a.tip * beta[i] * beta[i];
-  double ll = 0.0, lp = 0.0;
-  for (int m = 0; m < k; ++m) ll += 0.5 * a.n_var[m] * log(tau[m]) - 0.5 * tau[m] * RS[m];
-  for (int i = 0; i < d; ++i) lp -= th[i] * th[i] / (2.0 * a.pvar);
-  double f = 0.5 * ldp - 0.5 * ldc - 0.5 * quad + ll + lp;
-  int failc = *r.failc, failp = *r.failp;
-  out[0] = f;
+  const int d = a.d;
   double* parts = out + 1 + d;
-  parts[0] = ldp; parts[1] = ldc; parts[2] = quad; parts[3] = ll; parts[4] = lp; parts[5] = f;
-  parts[6] = failc; parts[7] = failp;
   double* ph = parts + kOutParts;
   const int tau0 = d - k;
-  for (int kp = 0; kp < d; ++kp) {
+  const int nterm = kk * kNJ * kNS;
+  if (warp == 0) {
+    // (3) f of Eq. 1
+    double quad = 0.0;
+    for (int i = lane; i < nterm; i += 32) {
+      const int pq = i / (kNJ * kNS), j = (i / kNS) % kNJ, s = i % kNS;
+      quad = fma(coef[i], RX[j][pq][s], quad);
+    }
+    const double* beta = r.x + (int64_t)nt * a.ld;
+    for (int i = lane; i < a.a; i += 32) quad += a.tip * beta[i] * beta[i];
+    quad = warp_total(quad);
+    if (lane == 0) {
+      const double ldc = SL[0], ldp = SL[1] + a.a * log(a.tip);
+      double ll = 0.0, lp = 0.0;
+      for (int m = 0; m < k; ++m) ll += 0.5 * a.n_var[m] * log(tau[m]) - 0.5 * tau[m] * RS[m];
+      for (int i = 0; i < d; ++i) lp -= th[i] * th[i] / (2.0 * a.pvar);
+      const double f = 0.5 * ldp - 0.5 * ldc - 0.5 * quad + ll + lp;
+      out[0] = f;
+      parts[0] = ldp; parts[1] = ldc; parts[2] = quad; parts[3] = ll; parts[4] = lp;
+      parts[5] = f;
+      parts[6] = *r.failc; parts[7] = *r.failp;
+    }
+  } else {
+    // (4) the gradient components of Eq. 6: one warp per component
+    for (int kp = warp - 1; kp < d; kp += nw - 1) {
     double trc = 0.0, trp = 0.0, qx = 0.0;
     if (a.grad) {
-      const double* dc = dcoef + (int64_t)kp * kk * kNJ * kNS;
-      for (int pq = 0; pq < kk; ++pq)
-        for (int j = 0; j < kNJ; ++j)
-          for (int s = 0; s < kNS; ++s) {
-            double w = dc[(pq * kNJ + j) * kNS + s];
-            trc += w * RDc[j][pq][s];
-            trp += w * RDp[j][pq][s];
-            qx += w * RX[j][pq][s];
-          }
+      const double* dc = dcoef + (int64_t)kp * nterm;
+      for (int i = lane; i < nterm; i += 32) {
+        const int pq = i / (kNJ * kNS), j = (i / kNS) % kNJ, s = i % kNS;
+        const double w = dc[i];
+        trc = fma(w, RDc[j][pq][s], trc);
+        trp = fma(w, RDp[j][pq][s], trp);
+        qx = fma(w, RX[j][pq][s], qx);
+      }
+      trc = warp_total(trc);
+      trp = warp_total(trp);
+      qx = warp_total(qx);
     }
-    double expl = -th[kp] / a.pvar;
-    if (kp >= tau0) {
-      int m = kp - tau0;
-      trc += tau[m] * (CNT[m] + 2.0 * PC[m] + TT[m]);
-      expl += 0.5 * a.n_var[m] - 0.5 * tau[m] * RS[m];
+    if (lane == 0) {
+      double expl = -th[kp] / a.pvar;
+      if (kp >= tau0) {
+        const int m = kp - tau0;
+        trc += tau[m] * (CNT[m] + 2.0 * PC[m] + TT[m]);
+        expl += 0.5 * a.n_var[m] - 0.5 * tau[m] * RS[m];
+      }
+      const double pa = -0.5 * trc, pb = -0.5 * qx, pcc = 0.5 * trp;
+      ph[kp] = pa;
+      ph[d + kp] = pb;
+      ph[2 * d + kp] = pcc;
+      ph[3 * d + kp] = expl;
+      out[1 + kp] = a.grad ? pa + pb + pcc + expl : 0.0;
     }
-    double pa = -0.5 * trc, pb = -0.5 * qx, pcc = 0.5 * trp;
-    ph[kp] = pa;
-    ph[d + kp] = pb;
-    ph[2 * d + kp] = pcc;
-    ph[3 * d + kp] = expl;
-    out[1 + kp] = a.grad ? pa + pb + pcc + expl : 0.0;
+    }
   }
 }
 
@@ -334,7 +377,7 @@ bta_status launch_finalize(const ModelDev& md, const CoefLayout& L, const double
   a.m_diag = md.m_diag; a.m_sub = md.m_sub; a.traw = md.traw;
   for (int m = 0; m < kMaxK; ++m) a.n_var[m] = m < md.k ? md.n_per_var[m] : 0.0;
   a.L = L; a.r = r;
-  finalize_kernel<<<1, RT, 0, s>>>(a, coefbuf, out);
+  finalize_kernel<<<1, kFinThreads, 0, s>>>(a, coefbuf, out);
   BTA_LAUNCHED();
   return BTA_OK;
 }
