@@ -233,9 +233,10 @@ def run_batch(args, P, torch, workloads):
         m.close()
 
 
-def run_step(args, model, theta, torch, stream):
+def run_step(args, prob, model, theta, torch, stream):
     """Value-and-gradient steps at one precision (0 FP64, 1 mixed, 2 emulated
-    FP64), the timed ones inside the profiler range (for launch lists)."""
+    FP64), the timed ones inside the profiler range (for launch lists); then,
+    outside it, the 2d+1 value-only evaluations of the FD gradient."""
     for _ in range(args.warmup):
         model.value_and_grad(theta, precision=args.precision)
     torch.cuda.synchronize()
@@ -247,8 +248,27 @@ def run_step(args, model, theta, torch, stream):
     e1.record(stream)
     e1.synchronize()
     torch.cuda.cudart().cudaProfilerStop()
-    print(json.dumps({"mode": "step", "precision": args.precision,
-                      "ms_per_step": e0.elapsed_time(e1) / args.steps, "f": f}), flush=True)
+    ms = e0.elapsed_time(e1) / args.steps
+    flops, fwd = _flops_model(prob.b, prob.nt, prob.a)
+    out = {"mode": "step", "workload": args.workload, "b": prob.b, "nt": prob.nt,
+           "precision": args.precision, "ms_per_step": ms, "f": f,
+           "algorithmic_tflop_per_step": flops / 1e12,
+           "tflops_fp64_equivalent": flops / ms / 1e9,
+           "frac_of_fp64_peak": flops / ms / 1e9 / FP64_PEAK_TFLOPS}
+    if args.step_fd:
+        d = len(theta)
+        pts = [theta] + [theta + s * 1e-3 * np.eye(d)[j] for j in range(d) for s in (1.0, -1.0)]
+        model.value_and_grad(theta, grad=False, precision=args.precision)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for q in pts:
+            model.value_and_grad(q, grad=False, precision=args.precision)
+        e1.record(stream)
+        e1.synchronize()
+        fd_ms = e0.elapsed_time(e1)
+        out.update({"fd_ms_per_gradient": fd_ms, "speedup_ad_vs_fd": fd_ms / ms,
+                    "c_ad": ms / (fd_ms / len(pts))})
+    print(json.dumps(out), flush=True)
 
 
 def main():
@@ -271,9 +291,14 @@ def main():
                     help="gemm: only the dominant kernel at the sweep's block shape "
                          "(the small case used for ncu captures); step: only the timed "
                          "value-and-gradient steps at --precision, inside the profiler range")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    help="step mode: the synthetic model (a name from workloads.WORKLOADS)")
+    ap.add_argument("--step-fd", action="store_true",
+                    help="step mode: also time the 2d+1 value-only evaluations of FD")
     args = ap.parse_args()
-    if args.warmup < 3:
+    if args.warmup < 3 and args.mode == "full":
         args.warmup = 3
+    args.warmup = max(args.warmup, 1)
     if args.impl == "reference":
         return run_reference(args)
 
@@ -303,12 +328,13 @@ def main():
                           "tflops_fp64_equivalent": tf}), flush=True)
         return
 
-    prob = workloads.make_problem(WORKLOAD, **({"nt": args.nt} if args.nt else {}))
+    prob = workloads.make_problem(args.workload if args.mode == "step" else WORKLOAD,
+                                  **({"nt": args.nt} if args.nt else {}))
     model = P.InlaModel(prob)
     theta = prob.theta.copy()
     stream = torch.cuda.current_stream()
     if args.mode == "step":
-        return run_step(args, model, theta, torch, stream)
+        return run_step(args, prob, model, theta, torch, stream)
     # warm-up (also captures the CUDA graphs)
     for _ in range(args.warmup):
         f, g = model.value_and_grad(theta)

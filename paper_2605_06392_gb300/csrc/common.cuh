@@ -166,6 +166,16 @@ bta_status potrf_inv_batch(int count, double* const* A, int n, int ld, double* c
                            double* const* logdet_parts, int32_t* const* fail,
                            const int32_t* fail_code, cudaStream_t s);
 int potrf_inv_slots(int n);   // number of logdet slots potrf_inv writes
+// The same with the precision of the sweep: above potrf_hybrid_leaf(precision)
+// rows the block is split 2 x 2 recursively, the diagonal sub-blocks factored
+// by the task-graph kernel and the products of each level run in FP64
+// (precision 0) or emulated FP64 (precision 1, 2; per-block workspace tcws of
+// ozaki_ws_bytes(n, n, n, 8) bytes and status words tcstat).
+bta_status potrf_inv_batch_prec(int count, double* const* A, int n, int ld,
+                                double* const* scratch, double* const* logdet_parts,
+                                int32_t* const* fail, const int32_t* fail_code, int precision,
+                                void* const* tcws, int32_t* const* tcstat, cudaStream_t s);
+int potrf_hybrid_leaf(int precision);
 // The task-graph kernel (potrf_dag.cu) used by potrf_inv_batch for n <= 5120;
 // g_potrf_recursive = 1 selects the recursive launch sequence instead.
 bta_status potrf_dag_batch(int count, double* const* A, int n, int ld, double* const* scratch,

@@ -15,6 +15,7 @@
 //                   (L^{-1})21 = -L22^{-1} L21 L11^{-1}
 // with a single-CTA shared-memory kernel for 32 x 32 leaves.
 #include <cmath>
+#include <cstdlib>
 
 #include "common.cuh"
 
@@ -206,7 +207,151 @@ bta_status rec(const PB& b, int64_t aoff, int n, int ld, int64_t woff, int soff,
   return BTA_OK;
 }
 
+// The products of one recursion level: batched FP64 (precision 0) or one
+// emulated-FP64 product per block (8 BF16 slices; FP64 accuracy).
+struct ProdCfg {
+  int precision = 0;
+  void* const* tcws = nullptr;
+  int32_t* const* tcstat = nullptr;
+};
+
+bta_status level_product(const Gemm& g, const ProdCfg& c, cudaStream_t s) {
+  if (c.precision == 0) return gemm_f64(g, s);
+  for (int z = 0; z < g.batch; ++z) {
+    Gemm one = g;
+    one.batch = 1;
+    one.Ab = nullptr; one.Bb = nullptr; one.Cb = nullptr; one.Cinb = nullptr;
+    one.A = g.Ab[z]; one.B = g.Bb[z]; one.C = g.Cb[z];
+    one.Cin = g.Cinb ? g.Cinb[z] : g.Cb[z];
+    BTA_TRY(ozaki_gemm(one, c.tcws[z], c.tcstat[z], 8, s));
+  }
+  return BTA_OK;
+}
+
+// The 2 x 2 recursion of rec() above, stopped at blocks of at most `leaf`
+// rows, which the task-graph kernel factors and inverts.  Those blocks hold
+// a fraction (leaf / n)^2 of the b^3 / 3 + b^3 / 3 flops of the factor and
+// the inverse; the rest are the four products of each level.
+bta_status rec_hybrid(const PB& b, int64_t aoff, int n, int ld, int64_t woff, int soff,
+                      int leaf, const ProdCfg& pc, cudaStream_t s) {
+  const int cnt = b.cnt;
+  if (n <= leaf) {
+    double* A[kMaxBatch];
+    double* W[kMaxBatch];
+    double* sl[kMaxBatch];
+    for (int z = 0; z < cnt; ++z) {
+      A[z] = b.A[z] + aoff;
+      W[z] = b.W[z] + woff;
+      sl[z] = b.slots[z] + soff;
+    }
+    return potrf_dag_batch(cnt, A, n, ld, W, sl, b.fail, b.code, s);
+  }
+  const int p = n / T;
+  const int n1 = (p / 2) * T, n2 = n - n1;
+  const int64_t o11 = aoff, o21 = aoff + n1, o22 = aoff + n1 + (int64_t)n1 * ld;
+  const int64_t w1 = woff, w2 = woff + (int64_t)n2 * n1;   // L21, L21 L11^{-1}
+  const int64_t wsub = w2 + (int64_t)n2 * n1;              // scratch of the recursion
+  const double* A11[kMaxBatch];
+  const double* A22c[kMaxBatch];
+  const double* A21c[kMaxBatch];
+  double* A21[kMaxBatch];
+  double* A22[kMaxBatch];
+  double* W1[kMaxBatch];
+  double* W2[kMaxBatch];
+  const double* W1c[kMaxBatch];
+  const double* W2c[kMaxBatch];
+  for (int z = 0; z < cnt; ++z) {
+    A11[z] = b.A[z] + o11;
+    A21[z] = b.A[z] + o21;
+    A21c[z] = A21[z];
+    A22[z] = b.A[z] + o22;
+    A22c[z] = A22[z];
+    W1[z] = b.W[z] + w1;
+    W2[z] = b.W[z] + w2;
+    W1c[z] = W1[z];
+    W2c[z] = W2[z];
+  }
+  BTA_TRY(rec_hybrid(b, o11, n1, ld, wsub, soff, leaf, pc, s));
+  {  // L21 = A21 * (L11^{-1})^T
+    Gemm g; g.M = n2; g.N = n1; g.K = n1; g.batch = cnt;
+    g.Ab = A21c; g.lda = ld;
+    g.Bb = A11; g.ldb = ld; g.transB = 1; g.triB = TRI_UPPER;
+    g.Cb = W1; g.ldc = n2;
+    BTA_TRY(level_product(g, pc, s));
+  }
+  {  // A22 -= L21 L21^T (lower)
+    Gemm g; g.M = n2; g.N = n2; g.K = n1; g.batch = cnt;
+    g.Ab = W1c; g.lda = n2;
+    g.Bb = W1c; g.ldb = n2; g.transB = 1;
+    g.Cb = A22; g.ldc = ld; g.Cinb = A22c; g.ldcin = ld;
+    g.alpha = -1.0; g.beta = 1.0; g.out_lower = 1;
+    BTA_TRY(level_product(g, pc, s));
+  }
+  BTA_TRY(rec_hybrid(b, o22, n2, ld, wsub, soff + n1 / T, leaf, pc, s));
+  {  // W2 = L21 * L11^{-1}
+    Gemm g; g.M = n2; g.N = n1; g.K = n1; g.batch = cnt;
+    g.Ab = W1c; g.lda = n2;
+    g.Bb = A11; g.ldb = ld; g.triB = TRI_LOWER;
+    g.Cb = W2; g.ldc = n2;
+    BTA_TRY(level_product(g, pc, s));
+  }
+  {  // (L^{-1})21 = -L22^{-1} W2
+    Gemm g; g.M = n2; g.N = n1; g.K = n2; g.batch = cnt;
+    g.Ab = A22c; g.lda = ld; g.triA = TRI_LOWER;
+    g.Bb = W2c; g.ldb = n2;
+    g.Cb = A21; g.ldc = ld; g.alpha = -1.0;
+    BTA_TRY(level_product(g, pc, s));
+  }
+  return BTA_OK;
+}
+
+int env_int(const char* name, int dflt) {
+  const char* v = std::getenv(name);
+  return v && *v ? std::atoi(v) : dflt;
+}
+
 }  // namespace
+
+int potrf_hybrid_leaf(int precision) {
+  // Largest block the task-graph kernel factors whole (0: always whole).
+  // Up to 1024 rows its serial chain of 32-row pivots costs about as much
+  // as the split's extra launches; above, the split wins (measured on GB300:
+  // b = 2025 1.6x (emulated) and 1.9x (mixed) faster per gradient, b = 4800
+  // 2.2x; FP64 b = 2025 1.4 %).
+  static const int fp64 = env_int("BTA_POTRF_LEAF_FP64", 1024);
+  static const int tc = env_int("BTA_POTRF_LEAF_TC", 1024);
+  return precision == 0 ? fp64 : tc;
+}
+
+bta_status potrf_inv_batch_prec(int count, double* const* A, int n, int ld,
+                                double* const* scratch, double* const* logdet_parts,
+                                int32_t* const* fail, const int32_t* fail_code, int precision,
+                                void* const* tcws, int32_t* const* tcstat, cudaStream_t s) {
+  if (n <= 0 || n % T || count < 0) return BTA_ERR_ARG;
+  const int leaf = potrf_hybrid_leaf(precision);
+  bool tc_ok = precision == 0 || (tcws && tcstat && n <= 5120);
+  for (int z = 0; tc_ok && precision != 0 && z < count; ++z) tc_ok = tcws[z] && tcstat[z];
+  if (leaf < T || n <= leaf || !tc_ok || n / T > 160 || g_potrf_recursive)
+    return potrf_inv_batch(count, A, n, ld, scratch, logdet_parts, fail, fail_code, s);
+  PriorityScope prio(highest_priority());
+  ProdCfg pc;
+  pc.precision = precision;
+  for (int z0 = 0; z0 < count; z0 += kMaxBatch) {
+    PB b;
+    b.cnt = count - z0 < kMaxBatch ? count - z0 : kMaxBatch;
+    for (int z = 0; z < b.cnt; ++z) {
+      b.A[z] = A[z0 + z];
+      b.W[z] = scratch[z0 + z];
+      b.slots[z] = logdet_parts[z0 + z];
+      b.fail[z] = fail[z0 + z];
+      b.code[z] = fail_code[z0 + z];
+    }
+    pc.tcws = tcws ? tcws + z0 : nullptr;
+    pc.tcstat = tcstat ? tcstat + z0 : nullptr;
+    BTA_TRY(rec_hybrid(b, 0, n, ld, 0, 0, (leaf / T) * T, pc, s));
+  }
+  return BTA_OK;
+}
 
 int potrf_inv_slots(int n) { return n / T; }
 

@@ -338,8 +338,14 @@ bta_status factor_sweep_multi(const SweepItem* it, int m, cudaStream_t s, cudaEv
       std::vector<int32_t*> fl;
       std::vector<int32_t> code(M, i);
       for (int z : G.all) fl.push_back(it[z].fail);
-      BTA_TRY(potrf_inv_batch(M, Di.data(), ld, ld, W.data(), sl.data(), fl.data(), code.data(),
-                              s));
+      std::vector<void*> tw;
+      std::vector<int32_t*> ts;
+      for (int z : G.all) {
+        tw.push_back(it[z].ws.tc);
+        ts.push_back(it[z].ws.tcstat);
+      }
+      BTA_TRY(potrf_inv_batch_prec(M, Di.data(), ld, ld, W.data(), sl.data(), fl.data(),
+                                   code.data(), precision, tw.data(), ts.data(), s));
       if (i == 0 && mark) BTA_CUDA_TRY(cudaEventRecord(mark, s));
     }
     for (const auto& grp : G.arrow) {  // L_Ci = C_i L_Di^{-T};  T -= L_Ci L_Ci^T
