@@ -293,6 +293,8 @@ def main():
                          "value-and-gradient steps at --precision, inside the profiler range")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="step mode: the synthetic model (a name from workloads.WORKLOADS)")
+    ap.add_argument("--gemm-n", type=int, default=0,
+                    help="gemm mode: the product's size n (n x n x n; default the block size)")
     ap.add_argument("--step-fd", action="store_true",
                     help="step mode: also time the 2d+1 value-only evaluations of FD")
     args = ap.parse_args()
@@ -320,7 +322,7 @@ def main():
     if args.mode == "batch":
         return run_batch(args, P, torch, workloads)
     if args.mode == "gemm":
-        b = workloads.WORKLOADS[WORKLOAD]["nx"] * workloads.WORKLOADS[WORKLOAD]["ny"]
+        b = args.gemm_n or workloads.WORKLOADS[WORKLOAD]["nx"] * workloads.WORKLOADS[WORKLOAD]["ny"]
         ms, tf = gemm_roofline(P, torch, b, reps=args.steps, mixed=args.precision)
         name = {0: "gemm_f64_kernel", 1: "tc_gemm_tf32x3_kernel (+ split)",
                 2: "ozaki_gemm_kernel<8> (+ split)"}[args.precision]

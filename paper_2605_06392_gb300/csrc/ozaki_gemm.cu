@@ -47,6 +47,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstdlib>
 
 #include "common.cuh"
 #include "tma.cuh"
@@ -176,6 +177,21 @@ __device__ __forceinline__ int bar_or_128(int v) {
   return r;
 }
 
+// alpha and beta as integer modes (decided on the host: comparisons of
+// doubles would run on the FP64 pipe once per element): alpha 0 -> +1,
+// 1 -> -1, 2 -> general; beta 0 -> 0, 1 -> +1, 2 -> general.
+inline int alpha_mode(double a) { return a == 1.0 ? 0 : a == -1.0 ? 1 : 2; }
+inline int beta_mode(double b) { return b == 0.0 ? 0 : b == 1.0 ? 1 : 2; }
+
+__device__ __forceinline__ double scale_add(double out, int am, double alpha, int bm, double beta,
+                                            const double* cin) {
+  if (am == 1) out = -out;
+  else if (am == 2) out *= alpha;
+  if (bm == 1) out += *cin;
+  else if (bm == 2) out = fma(beta, *cin, out);
+  return out;
+}
+
 // X * 2^E rounded to the nearest double, from the integer X by integer
 // operations (the usual case); out-of-range exponents take ldexp.
 __device__ __forceinline__ double compose(long long X, int E) {
@@ -199,6 +215,7 @@ __device__ __forceinline__ double compose(long long X, int E) {
 struct OzArgs {
   int M, N, Kp, Mp, Np;
   double alpha, beta;
+  int amode, bmode;
   double* C;
   int ldc;
   const double* Cin;
@@ -376,10 +393,8 @@ __global__ void __maxnreg__(248)
             const long long X = acc[q] + __float2ll_rn(v[q] * 34359738368.0f);
             // a = 2^(exA - 1029) sum_j A_j, b likewise: C = X 2^(exA + exB - 2058 - 35)
             double out = compose(X, ea + s_exB[cc * 32 + q] - 2093);
-            if (g.alpha == -1.0) out = -out;
-            else if (g.alpha != 1.0) out *= g.alpha;
-            if (g.beta == 1.0) out += g.Cin[m + (int64_t)n * g.ldcin];
-            else if (g.beta != 0.0) out = fma(g.beta, g.Cin[m + (int64_t)n * g.ldcin], out);
+            out = scale_add(out, g.amode, g.alpha, g.bmode, g.beta,
+                            g.Cin + m + (int64_t)n * g.ldcin);
             g.C[m + (int64_t)n * g.ldc] = out;
           }
         }
@@ -403,6 +418,374 @@ __global__ void __maxnreg__(248)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(Cfg::kTmemCols)
                  : "memory");
+  }
+}
+
+// ---- 128 x 128 tiles (S = 8) ----------------------------------------------------
+//
+// The same products with N = 128 MMAs, which take as long as N = 64 ones: a
+// 128 x 128 tile per CTA doubles the work per MMA.  Tensor memory (512
+// columns) then holds four 128-column accumulators, not seven, so every
+// 512-wide K chunk runs four sub-passes over its 16 slabs, each streaming
+// four A and four B slices (64 KB a slab, a 3-stage ring):
+//   P0  levels 2..5   A1..4 x B1..4, j + l <= 5      4 exact accumulators
+//   P1  levels 6..9   A1..4 x B5..8                  levels 6, 7 exact + rounded
+//   P2  levels 6..8   A1..4 x B1..4, 6 <= j + l <= 8 (the same three)
+//   P3  levels 6..9   A5..8 x B1..4                  (the same three)
+// (10 + 10 + 6 + 10 = 36 pairs).  The accumulators are drained after P0 and
+// after P3 into the 64-bit integer sum of the tile, kept in the workspace;
+// the rounded one is drained per chunk too (one rounding to 2^-35 of the
+// level-2 unit per chunk).  K chunks may be split over several CTAs (grid
+// z), each with its own integer sums; ozaki_compose_kernel adds them and
+// assembles C.  576 threads: warps 0-15 drain (four per TMEM lane quarter,
+// 32 columns each, the tile's 64-bit sums held in their registers across
+// the chunks, so a drain is TMEM loads and integer adds only), warp 16
+// loads, warp 17 issues MMAs.
+constexpr int QN = 128;
+constexpr int kQThreads = 576;
+constexpr int kQDrain = 512;
+constexpr int kQTile = 128 * OK16 * 2;    // one slice slab: 128 rows x 32 of K, 8 KB
+constexpr int kQStage = 8 * kQTile;       // 4 A slots + 4 B slots: 64 KB
+constexpr int kQStages = 3;
+constexpr int kQPasses = 4;
+constexpr int kQSmem = kQStages * kQStage + 1024 + 256;
+constexpr uint32_t kQIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(QN >> 3) << 17) |
+                             ((uint32_t)(OM >> 4) << 24);
+
+// First A and B slice (0-based) a sub-pass streams.
+__host__ __device__ constexpr int q_a0(int P) { return P == 3 ? 4 : 0; }
+__host__ __device__ constexpr int q_b0(int P) { return P == 1 ? 4 : 0; }
+
+// MMA of A slot I and B slot LL in sub-pass P for the 16-wide K step KK.
+template <int P, int I, int LL, int KK>
+__device__ __forceinline__ void q_pair(uint32_t tmem, uint64_t dst, uint32_t first,
+                                       uint32_t leader) {
+  constexpr int L = q_a0(P) + I + q_b0(P) + LL + 2;   // level
+  constexpr bool kValid = P == 0 ? L <= 5 : (P == 2 ? (L >= 6 && L <= 8) : L <= 9);
+  if constexpr (kValid) {
+    constexpr int kAcc = P == 0 ? L - 2 : (L <= 7 ? L - 6 : 2);
+    // P0 and P1 open their accumulator set (P1's levels 6, 7, 8 come first)
+    constexpr bool kMayOpen = KK == 0 && I == 0 && (P == 0 || (P == 1 && L <= 8));
+    const uint32_t accumulate = kMayOpen ? (first ? 0u : 1u) : 1u;
+    constexpr unsigned long long kAo = (unsigned long long)(I * kQTile + KK * 32) >> 4;
+    constexpr unsigned long long kBo = (unsigned long long)((4 + LL) * kQTile + KK * 32) >> 4;
+    asm volatile(
+        "{\n .reg .b64 da, db;\n .reg .pred p, e;\n"
+        " add.s64 da, %1, %2;\n add.s64 db, %1, %3;\n"
+        " setp.ne.b32 p, %5, 0;\n setp.ne.b32 e, %6, 0;\n"
+        " @e tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %4, p;\n}\n" ::"r"(
+            tmem + (uint32_t)(kAcc * QN)),
+        "l"(dst), "n"(kAo), "n"(kBo), "r"(kQIdesc), "r"(accumulate), "r"(leader)
+        : "memory");
+  }
+}
+
+template <int P, int I, int LL, int KK>
+__device__ __forceinline__ void q_row(uint32_t tmem, uint64_t dst, uint32_t first,
+                                      uint32_t leader) {
+  if constexpr (LL < 4) {
+    q_pair<P, I, LL, KK>(tmem, dst, first, leader);
+    q_row<P, I, LL + 1, KK>(tmem, dst, first, leader);
+  }
+}
+
+template <int P, int I, int KK>
+__device__ __forceinline__ void q_step(uint32_t tmem, uint64_t dst, uint32_t first,
+                                       uint32_t leader) {
+  if constexpr (I < 4) {
+    q_row<P, I, 0, KK>(tmem, dst, first, leader);
+    q_step<P, I + 1, KK>(tmem, dst, first, leader);
+  }
+}
+
+template <int P>
+__device__ __forceinline__ void q_slab(uint32_t tmem, uint64_t dst, uint32_t first,
+                                       uint32_t leader) {
+  q_step<P, 0, 0>(tmem, dst, first, leader);
+  q_step<P, 0, 1>(tmem, dst, first, leader);
+}
+
+// OR of v over the 512 threads of warps 0-15 (named barrier 1).
+__device__ __forceinline__ int bar_or_512(int v) {
+  int r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.s32 p, %1, 0;\n"
+      " barrier.cta.red.or.pred q, 1, 512, p;\n selp.s32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"(v)
+      : "memory");
+  return r;
+}
+
+struct OzqArgs {
+  int Mp, Np, Bp, nk, nchunks, splits;   // Bp: rows per B slice in its array
+  int group;                             // tile rows per group of the launch order
+  int out_lower;
+  long long* partial;   // [splits][Np][Mp] integer sums, units 2^-35 of level 2
+  int32_t* status;
+};
+
+// 16 consecutive fp32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+      "%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// 8 consecutive fp32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// 18 warps: an SM sub-partition hosts five of them, so at most 96
+// registers a thread (5 x 32 x 96 <= 16 K).
+__global__ void __launch_bounds__(kQThreads, 1)
+    ozaki_gemm128_kernel(const __grid_constant__ CUtensorMap mA,
+                         const __grid_constant__ CUtensorMap mB, OzqArgs g) {
+  // Tile order: groups of `group` tile rows, column by column inside a
+  // group, so that the CTAs resident together share few A and B row blocks.
+  const int mt_all = g.Mp / OM, nt_all = g.Np / QN;
+  const int grp = (int)blockIdx.x / (g.group * nt_all);
+  const int gm = min(g.group, mt_all - grp * g.group);
+  const int in = (int)blockIdx.x - grp * g.group * nt_all;
+  const int m0 = (grp * g.group + in % gm) * OM, n0 = (in / gm) * QN, z = blockIdx.z;
+  if (g.out_lower && n0 > m0 + OM - 1) return;   // whole CTA exits before any set-up
+  const int c0 = (int)((int64_t)z * g.nchunks / g.splits);
+  const int c1 = (int)((int64_t)(z + 1) * g.nchunks / g.splits);
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kQStages * kQStage);
+  const int kFull = 0, kEmpty = kQStages, kAccFull = 2 * kQStages,
+            kAccEmpty = 2 * kQStages + 1, kFinal = 2 * kQStages + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kQStages + 3);
+  __shared__ int s_abort, s_issued, s_consumed;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kQStages; ++s) {
+      mbar_init(smem_u32(&bars[kFull + s]), 1);
+      mbar_init(smem_u32(&bars[kEmpty + s]), 1);
+    }
+    mbar_init(smem_u32(&bars[kAccFull]), 1);
+    mbar_init(smem_u32(&bars[kAccEmpty]), kQDrain);
+    mbar_init(smem_u32(&bars[kFinal]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_abort = 0;
+    s_issued = 0;
+    s_consumed = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 16) {
+    // ---- TMA producer: for each chunk and sub-pass, the chunk's slabs of the
+    // sub-pass's slices; ring position r = running slab count
+    const uint32_t leader = lane == 0;
+    int r = 0;
+    bool stop = false;
+    for (int c = c0; c < c1 && !stop; ++c) {
+      const int kt0 = c * kChunkSlabs, kt1 = min(g.nk, kt0 + kChunkSlabs);
+      for (int P = 0; P < kQPasses && !stop; ++P) {
+        const int aj0 = q_a0(P), bl0 = q_b0(P);
+        for (int kt = kt0; kt < kt1; ++kt, ++r) {
+          const int s = r % kQStages;
+          if (r >= kQStages &&
+              !warp_wait(smem_u32(&bars[kEmpty + s]), (uint32_t)((r / kQStages - 1) & 1), lane)) {
+            if (leader) atomicExch(&s_abort, 1);
+            stop = true;
+            break;
+          }
+          if (warp_flag(&s_abort, lane)) {
+            stop = true;
+            break;
+          }
+          if (leader) {
+            const uint32_t full = smem_u32(&bars[kFull + s]);
+            mbar_expect_tx(full, (uint32_t)kQStage);
+            uint8_t* st = smem + s * kQStage;
+            const int k0 = kt * OK16;
+            for (int i = 0; i < 4; ++i)
+              tma_load_2d(smem_u32(st + i * kQTile), &mA, full, k0, (aj0 + i) * g.Mp + m0);
+            for (int l = 0; l < 4; ++l)
+              tma_load_2d(smem_u32(st + (4 + l) * kQTile), &mB, full, k0, (bl0 + l) * g.Bp + n0);
+            *(volatile int*)&s_issued = r + 1;
+          }
+          __syncwarp();
+        }
+      }
+    }
+  } else if (warp == 17) {
+    // ---- MMA issuer: the whole warp runs the loop, lane 0 issues
+    const uint32_t leader = lane == 0;
+    const uint64_t dbase = sdesc64(smem_u32(smem));
+    bool stop = false;
+    int r = 0, e = 0;   // slabs consumed, accumulator sets handed to the drain
+    for (int c = c0; c < c1 && !stop; ++c) {
+      const int kt0 = c * kChunkSlabs, kt1 = min(g.nk, kt0 + kChunkSlabs);
+      for (int P = 0; P < kQPasses && !stop; ++P) {
+        // P0 and P1 open an accumulator set: wait until the previous one is drained
+        if (P <= 1 && e > 0 &&
+            !warp_wait(smem_u32(&bars[kAccEmpty]), (uint32_t)((e - 1) & 1), lane)) {
+          stop = true;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        for (int kt = kt0; kt < kt1; ++kt, ++r) {
+          const int s = r % kQStages;
+          if (warp_flag(&s_abort, lane) ||
+              !warp_wait(smem_u32(&bars[kFull + s]), (uint32_t)((r / kQStages) & 1), lane)) {
+            stop = true;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint64_t dst = dbase + (uint64_t)((s * kQStage) >> 4);
+          const uint32_t first = kt == kt0;
+          if (P == 0) q_slab<0>(tmem, dst, first, leader);
+          else if (P == 1) q_slab<1>(tmem, dst, first, leader);
+          else if (P == 2) q_slab<2>(tmem, dst, first, leader);
+          else q_slab<3>(tmem, dst, first, leader);
+          mma_commit_if(smem_u32(&bars[kEmpty + s]), leader);   // slab free once these finish
+          if (leader) *(volatile int*)&s_consumed = r + 1;
+          __syncwarp();
+        }
+        if (!stop && (P == 0 || P == kQPasses - 1)) {
+          mma_commit_if(smem_u32(&bars[kAccFull]), leader);   // this set's sums ready
+          ++e;
+        }
+      }
+    }
+    if (stop) {
+      if (leader) atomicExch(&s_abort, 1);
+      mma_commit_if(smem_u32(&bars[kFinal]), leader);
+      warp_wait(smem_u32(&bars[kFinal]), 0, lane);
+    }
+  } else {
+    // ---- warps 0-15: thread = output row (TMEM lane) x 32 columns; the
+    // tile's integer sums (units 2^-35 of the level-2 unit) stay in registers
+    const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+    const int row = (warp & 3) * 32 + lane, col0 = (warp >> 2) * 32;
+    long long acc[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) acc[q] = 0ll;
+    int failed = 0, e = 0;
+    for (int c = c0; c < c1 && !failed; ++c) {
+      for (int set = 0; set < 2; ++set, ++e) {
+        const bool ok = mbar_wait(smem_u32(&bars[kAccFull]), (uint32_t)(e & 1), kOzWaitLimit);
+        if (bar_or_512(!ok || *(volatile int*)&s_abort)) {
+          failed = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        float v[8];
+        if (set == 0) {
+          // levels 2..5
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            const float up = __int_as_float((127 + 7 * a) << 23);
+            const long long sc = 1ll << (7 * (5 - a));
+#pragma unroll
+            for (int hh = 0; hh < 4; ++hh) {
+              tmem_ld8(tmem + lane_off + (uint32_t)(a * QN + col0 + 8 * hh), v);
+#pragma unroll
+              for (int q = 0; q < 8; ++q)
+                acc[8 * hh + q] += (long long)__float2int_rn(v[q] * up) * sc;
+            }
+          }
+        } else {
+#pragma unroll
+          for (int hh = 0; hh < 4; ++hh) {
+            tmem_ld8(tmem + lane_off + (uint32_t)(0 * QN + col0 + 8 * hh), v);   // level 6
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+              acc[8 * hh + q] += (long long)__float2int_rn(v[q] * 268435456.0f) * 128ll;
+            tmem_ld8(tmem + lane_off + (uint32_t)(1 * QN + col0 + 8 * hh), v);   // level 7
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+              acc[8 * hh + q] += (long long)__float2int_rn(v[q] * 34359738368.0f);
+            tmem_ld8(tmem + lane_off + (uint32_t)(2 * QN + col0 + 8 * hh), v);   // levels 8, 9
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc[8 * hh + q] += __float2ll_rn(v[q] * 34359738368.0f);
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(smem_u32(&bars[kAccEmpty]));
+      }
+    }
+    if (!failed) {
+      long long* part = g.partial + (int64_t)z * g.Mp * g.Np + (m0 + row) +
+                        (int64_t)(n0 + col0) * g.Mp;
+#pragma unroll
+      for (int q = 0; q < 32; ++q) part[(int64_t)q * g.Mp] = acc[q];
+    }
+    if (failed && threadIdx.x == 0) atomicExch(&s_abort, 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x == 0 && s_abort) {
+    for (int r = s_consumed; r < s_issued; ++r)
+      mbar_wait(smem_u32(&bars[kFull + r % kQStages]), (uint32_t)((r / kQStages) & 1),
+                kOzWaitLimit);
+    if (g.status) atomicExch(g.status, (int)BTA_ERR_TIMEOUT);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512)
+                 : "memory");
+  }
+}
+
+// C = alpha * (sum over the splits of the integer tile sums) * 2^(exA + exB - 2093)
+// + beta * Cin; one thread per element, m fastest.
+struct ComposeArgs {
+  int M, N, Mp, Np, splits, out_lower;
+  double alpha, beta;
+  int amode, bmode;
+  double* C;
+  int ldc;
+  const double* Cin;
+  int ldcin;
+  const int* exA;
+  const int* exB;
+  const long long* partial;
+};
+
+__global__ void ozaki_compose_kernel(ComposeArgs g) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= g.M) return;
+  for (int n = blockIdx.y; n < g.N; n += gridDim.y) {
+    if (g.out_lower && m < n) break;
+    const long long* p = g.partial + m + (int64_t)n * g.Mp;
+    long long X = 0;
+    for (int z = 0; z < g.splits; ++z) X += p[(int64_t)z * g.Mp * g.Np];
+    double out = compose(X, g.exA[m] + g.exB[n] - 2093);
+    out = scale_add(out, g.amode, g.alpha, g.bmode, g.beta, g.Cin + m + (int64_t)n * g.ldcin);
+    g.C[m + (int64_t)n * g.ldc] = out;
   }
 }
 
@@ -486,20 +869,29 @@ __device__ __forceinline__ void digits(double v, int er, float (&out)[S]) {
     }
     if (bits >> 63) F = -F;
   }
+  // F = G 2^28 + R, R in [-2^27, 2^27): digits 1..4 from G, 5..8 from R,
+  // each taken with round-half-up so that every remainder stays within
+  // half a digit (|d_1| <= 128, |d_j| <= 64 otherwise); 32-bit arithmetic.
+  const int G0 = (int)((F + (1ll << 27)) >> 28);
+  const int R0 = (int)(F - (long long)G0 * (1ll << 28));
+  int parts[2] = {G0, R0};
 #pragma unroll
-  for (int j = 0; j < S; ++j) {
-    const int shj = 49 - 7 * j;   // digit j covers bits [shj, shj + 7) of F
-    long long d;
-    if (shj > 0) {
-      // nearest: d = floor((F + h) / 2^shj), remainder (F + h) mod 2^shj - h
-      const long long h = 1ll << (shj - 1);
-      const long long t = F + h;
-      d = t >> shj;
-      F = (t & ((1ll << shj) - 1)) - h;
-    } else {
-      d = F;
+  for (int hpart = 0; hpart < 2; ++hpart) {
+    int x = parts[hpart];
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      const int j = 4 * hpart + jj;
+      if (j >= S) break;
+      int d;
+      if (jj < 3) {
+        const int sh = 21 - 7 * jj;
+        d = (x + (1 << (sh - 1))) >> sh;
+        x -= d * (1 << sh);
+      } else {
+        d = x;
+      }
+      out[j] = (float)d * __int_as_float((127 - 7 * j) << 23);
     }
-    out[j] = (float)d * __int_as_float((127 - 7 * j) << 23);
   }
 }
 
@@ -559,12 +951,49 @@ bta_status make_map_bf16(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap* map
   return r == CUDA_SUCCESS ? BTA_OK : BTA_ERR_ARG;
 }
 
+// Which kernel a product takes: 128 x 64 tiles, or (S = 8) 128 x 128 tiles
+// with the K chunks split over `splits` CTAs per tile.  A wave model: the
+// CTA of either kernel takes about as long per 512 of K, so the time goes
+// as (waves of CTAs) x (chunks per CTA); the 128 x 128 kernel is taken
+// when that is smaller (BTA_OZAKI_N128 = 0 / 1 forces the choice).
+struct OzPlan {
+  bool n128 = false;
+  int splits = 1;
+};
+constexpr int kSmCount = 152;
+constexpr int kMaxSplits = 8;
+
+OzPlan oz_plan(int M, int N, int K, int S) {
+  static const int force = [] {
+    const char* v = std::getenv("BTA_OZAKI_N128");
+    return v && *v ? std::atoi(v) : -1;
+  }();
+  OzPlan p;
+  if (S != 8 || force == 0) return p;
+  const int64_t nch = cdiv(cdiv(K, OK16), kChunkSlabs);
+  const int64_t t64 = (int64_t)cdiv(M, OM) * cdiv(N, OBN);
+  const int64_t t128 = (int64_t)cdiv(M, OM) * cdiv(N, QN);
+  const int64_t est64 = cdiv(t64, kSmCount) * nch;
+  int64_t best = -1;
+  for (int sp = 1; sp <= kMaxSplits && sp <= nch; ++sp) {
+    if (sp > 1 && t128 * sp > kSmCount) break;   // keeps the split sums small
+    const int64_t est = cdiv(t128 * sp, kSmCount) * cdiv(nch, sp);
+    if (best < 0 || est < best) {
+      best = est;
+      p.splits = sp;
+    }
+  }
+  p.n128 = force == 1 || best < est64;
+  if (!p.n128) p.splits = 1;
+  return p;
+}
+
 struct OzLayout {
   int Mp, Np, Kp;
   size_t a_off, b_off, ea_off, eb_off, p_off, total;
-  OzLayout(int M, int N, int K, int S) {
+  OzLayout(int M, int N, int K, int S, const OzPlan& plan) {
     Mp = cdiv(M, OM) * OM;
-    Np = cdiv(N, OBN) * OBN;
+    Np = plan.n128 ? cdiv(N, QN) * QN : cdiv(N, OBN) * OBN;
     Kp = cdiv(K, OK16) * OK16;
     auto up = [](size_t x) { return (x + 255) / 256 * 256; };
     a_off = 0;
@@ -572,7 +1001,8 @@ struct OzLayout {
     ea_off = b_off + up((size_t)S * Np * Kp * 2);
     eb_off = ea_off + up((size_t)Mp * 4);
     p_off = eb_off + up((size_t)Np * 4);
-    const size_t part = Kp > kChunkSlabs * OK16 ? (size_t)Mp * Np * 8 : 0;
+    const size_t part = plan.n128 ? (size_t)plan.splits * Mp * Np * 8
+                                  : (Kp > kChunkSlabs * OK16 ? (size_t)Mp * Np * 8 : 0);
     total = p_off + up(part) + 256;
   }
 };
@@ -583,7 +1013,8 @@ bta_status launch_ozaki(const Gemm& g, uint8_t* ws, int32_t* status, cudaStream_
   PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
   BTA_TRY(tensor_map_encoder(&enc));
   const int M = g.M, N = g.N, K = g.K;
-  const OzLayout L(M, N, K, S);
+  const OzPlan plan = oz_plan(M, N, K, S);
+  const OzLayout L(M, N, K, S, plan);
   __nv_bfloat16* YA = reinterpret_cast<__nv_bfloat16*>(ws + L.a_off);
   __nv_bfloat16* YB = reinterpret_cast<__nv_bfloat16*>(ws + L.b_off);
   int* exA = reinterpret_cast<int*>(ws + L.ea_off);
@@ -609,7 +1040,38 @@ bta_status launch_ozaki(const Gemm& g, uint8_t* ws, int32_t* status, cudaStream_
   const int bpitch = same ? L.Mp : L.Np;   // rows per B slice in its array
   CUtensorMap mA, mB;
   BTA_TRY(make_map_bf16(enc, &mA, YA, S * L.Mp, L.Kp, OM));
-  BTA_TRY(make_map_bf16(enc, &mB, YBm, S * bpitch, L.Kp, OBN));
+  BTA_TRY(make_map_bf16(enc, &mB, YBm, S * bpitch, L.Kp, plan.n128 ? QN : OBN));
+  long long* partial = reinterpret_cast<long long*>(ws + L.p_off);
+  if (plan.n128) {
+    static bool attr128 = false;
+    if (!attr128) {
+      BTA_CUDA_TRY(cudaFuncSetAttribute(ozaki_gemm128_kernel,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, kQSmem));
+      attr128 = true;
+    }
+    OzqArgs q;
+    q.Mp = L.Mp; q.Np = L.Np; q.Bp = bpitch;
+    q.nk = L.Kp / OK16;
+    q.nchunks = cdiv(q.nk, kChunkSlabs);
+    q.splits = plan.splits;
+    q.out_lower = g.out_lower;
+    q.partial = partial;
+    q.status = status;
+    q.group = std::min(L.Mp / OM, 12);   // ~sqrt(152): a wave spans ~12 x 13 tiles
+    ozaki_gemm128_kernel<<<dim3((L.Mp / OM) * (L.Np / QN), 1, plan.splits), kQThreads, kQSmem,
+                           s>>>(mA, mB, q);
+    BTA_LAUNCHED();
+    ComposeArgs c;
+    c.M = M; c.N = N; c.Mp = L.Mp; c.Np = L.Np; c.splits = plan.splits;
+    c.out_lower = g.out_lower;
+    c.alpha = g.alpha; c.beta = g.beta; c.C = g.C; c.ldc = g.ldc;
+    c.amode = alpha_mode(g.alpha); c.bmode = beta_mode(g.beta);
+    c.Cin = g.Cin ? g.Cin : g.C; c.ldcin = g.Cin ? g.ldcin : g.ldc;
+    c.exA = exA; c.exB = same ? exA : exB; c.partial = partial;
+    ozaki_compose_kernel<<<dim3(cdiv(M, 256), std::min(N, 65535)), 256, 0, s>>>(c);
+    BTA_LAUNCHED();
+    return BTA_OK;
+  }
   static bool attr_set = false;
   if (!attr_set) {
     BTA_CUDA_TRY(cudaFuncSetAttribute(ozaki_gemm_kernel<S>,
@@ -619,9 +1081,10 @@ bta_status launch_ozaki(const Gemm& g, uint8_t* ws, int32_t* status, cudaStream_
   OzArgs a;
   a.M = M; a.N = N; a.Kp = L.Kp; a.Mp = L.Mp; a.Np = bpitch;
   a.alpha = g.alpha; a.beta = g.beta; a.C = g.C; a.ldc = g.ldc;
+  a.amode = alpha_mode(g.alpha); a.bmode = beta_mode(g.beta);
   a.Cin = g.Cin ? g.Cin : g.C; a.ldcin = g.Cin ? g.ldcin : g.ldc;
   a.out_lower = g.out_lower; a.exA = exA; a.exB = same ? exA : exB; a.status = status;
-  a.partial = reinterpret_cast<long long*>(ws + L.p_off);
+  a.partial = partial;
   ozaki_gemm_kernel<S><<<dim3(L.Mp / OM, L.Np / OBN), kOzThreads, Cfg::kSmem, s>>>(mA, mB, a);
   BTA_LAUNCHED();
   return BTA_OK;
@@ -629,8 +1092,18 @@ bta_status launch_ozaki(const Gemm& g, uint8_t* ws, int32_t* status, cudaStream_
 
 }  // namespace
 
+// An upper bound over every product of at most M x N x K (either kernel):
+// a sweep sizes one workspace for all of its products.
 size_t ozaki_ws_bytes(int M, int N, int K, int slices) {
-  return OzLayout(M, N, K, slices).total;
+  const size_t t64 = OzLayout(M, N, K, slices, OzPlan()).total;
+  if (slices != 8) return t64;
+  const size_t Mq = (size_t)cdiv(M, OM) * OM, Nq = (size_t)cdiv(N, QN) * QN;
+  const size_t Kp = (size_t)cdiv(K, OK16) * OK16;
+  auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+  const size_t part = std::max(Mq * Nq, (size_t)kSmCount * OM * QN) * 8;
+  const size_t t128 = up(8 * Mq * Kp * 2) + up(8 * Nq * Kp * 2) + up(Mq * 4) + up(Nq * 4) +
+                      up(part) + 256;
+  return std::max(t64, t128);
 }
 
 bool ozaki_supported(const Gemm& g) {

@@ -9,6 +9,11 @@ max_k|b_kn| (the truncated digits of both operands and the dropped pair
 levels) plus FP64 rounding of the result and of the host reference.  The whole evaluation in this mode must meet
 the FP64 path's bar against the oracle (relative 1e-10).
 """
+import json
+import os
+import subprocess
+import sys
+
 import numpy as np
 import pytest
 
@@ -131,3 +136,74 @@ def test_emulated_mode_value_backward_split(P):
     fv, _ = m.value_and_grad(prob.theta, grad=False, precision=2)
     assert fv == f1
     m.close()
+
+
+# ---- both GEMM kernels on every shape -------------------------------------
+# The kernel (128 x 64 tiles, or 128 x 128 tiles with split K) is chosen from
+# the shape; BTA_OZAKI_N128 = 0 / 1 forces it, read once per process, so each
+# forced run is a child process that reports max(error / bound) per shape.
+_SHAPES = [(1024, 1024, 1024, False, True), (300, 200, 700, False, False),
+           (130, 70, 33, True, False), (512, 256, 2048, True, True),
+           (256, 256, 5120, False, True), (640, 384, 1536, True, False)]
+
+
+def _child_gemm():
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import torch
+    import paper_2605_06392_gb300 as P
+    out = []
+    for M, N, K, ta, tb in _SHAPES:
+        g = torch.Generator().manual_seed(M + 3 * N + 7 * K)
+        A = torch.randn((M, K) if ta else (K, M), generator=g, dtype=torch.float64)
+        B = torch.randn((K, N) if tb else (N, K), generator=g, dtype=torch.float64)
+        C0 = torch.randn((N, M), generator=g, dtype=torch.float64)
+        C, opA, opB, c0 = _run(P, A.cuda(), B.cuda(), C0.cuda(), -1.0, 1.0, ta, tb, 8)
+        ref = c0 - opA @ opB
+        bound = (12.0 * 2.0 ** -56 * K * np.max(np.abs(opA), axis=1)[:, None]
+                 * np.max(np.abs(opB), axis=0)[None, :]
+                 + 4.0 * K * 2.0 ** -53 * (np.abs(opA) @ np.abs(opB) + np.abs(c0)))
+        out.append({"shape": [M, N, K], "ratio": float(np.max(np.abs(C - ref) / bound))})
+    gi = torch.Generator().manual_seed(11)
+    A = torch.randint(-100, 101, (1024, 384), generator=gi).double().cuda()
+    B = torch.randint(-100, 101, (640, 1024), generator=gi).double().cuda()
+    C0 = torch.randint(-1000, 1001, (640, 384), generator=gi).double().cuda()
+    C, opA, opB, c0 = _run(P, A, B, C0, -1.0, 1.0, False, False, 8)
+    exact = c0 - opA.astype(np.int64) @ opB.astype(np.int64)
+    # whole evaluations (the sweeps' lower-triangle and triangular-operand products)
+    evals = {}
+    for name in ("st_tiny", "coreg_small"):
+        prob = workloads.make_problem(name)
+        m = P.InlaModel(prob)
+        f, gr = m.value_and_grad(prob.theta, precision=2)
+        evals[name] = {"f": f, "g": np.asarray(gr).tolist(),
+                       "x": m.mode().cpu().numpy().tolist()}
+        m.close()
+    print("RESULT " + json.dumps({"shapes": out, "evals": evals,
+                                  "integer_exact": bool(np.array_equal(C, exact.astype(np.float64)))}),
+          flush=True)
+
+
+@pytest.mark.parametrize("force", ["0", "1"])
+def test_both_kernels_within_bound(P, force):
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, BTA_OZAKI_N128=force,
+               PYTHONPATH=os.pathsep.join([root, os.environ.get("PYTHONPATH", "")]))
+    r = subprocess.run([sys.executable, os.path.abspath(__file__)], env=env,
+                       capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stderr[-3000:]
+    res = json.loads([ln for ln in r.stdout.splitlines() if ln.startswith("RESULT ")][-1][7:])
+    assert res["integer_exact"]
+    for v in res["shapes"]:
+        assert v["ratio"] <= 1.0, v
+    from oracle import bta
+    for name, v in res["evals"].items():
+        o = bta.evaluate(workloads.make_problem(name))
+        scale = np.maximum(np.abs(o.grad),
+                           np.abs(o.phase_a) + np.abs(o.phase_b) + np.abs(o.phase_c))
+        assert abs(v["f"] - o.f) <= 1e-10 * abs(o.f), name
+        assert np.max(np.abs(np.array(v["g"]) - o.grad) / scale) <= 1e-10, name
+        assert np.max(np.abs(np.array(v["x"]) - o.x)) <= 1e-10 * np.max(np.abs(o.x)), name
+
+
+if __name__ == "__main__":
+    _child_gemm()

@@ -71,7 +71,8 @@ def built():
 def test_split_factor_against_oracle(built, leaf, names):
     from oracle import bta
     import workloads
-    env = dict(os.environ, BTA_POTRF_LEAF_FP64=str(leaf), BTA_POTRF_LEAF_TC=str(leaf))
+    env = dict(os.environ, BTA_POTRF_LEAF_FP64=str(leaf), BTA_POTRF_LEAF_TC=str(leaf),
+               PYTHONPATH=os.pathsep.join([ROOT, os.environ.get("PYTHONPATH", "")]))
     r = subprocess.run([sys.executable, os.path.abspath(__file__)] + names, env=env,
                        capture_output=True, text=True, timeout=900)
     assert r.returncode == 0, r.stderr[-3000:]
