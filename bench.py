@@ -251,6 +251,7 @@ def run_step(args, prob, model, theta, torch, stream):
     ms = e0.elapsed_time(e1) / args.steps
     flops, fwd = _flops_model(prob.b, prob.nt, prob.a)
     out = {"mode": "step", "workload": args.workload, "b": prob.b, "nt": prob.nt,
+           "low_memory": bool(args.low_memory),
            "precision": args.precision, "ms_per_step": ms, "f": f,
            "algorithmic_tflop_per_step": flops / 1e12,
            "tflops_fp64_equivalent": flops / ms / 1e9,
@@ -295,6 +296,8 @@ def main():
                     help="step mode: the synthetic model (a name from workloads.WORKLOADS)")
     ap.add_argument("--gemm-n", type=int, default=0,
                     help="gemm mode: the product's size n (n x n x n; default the block size)")
+    ap.add_argument("--low-memory", action="store_true",
+                    help="step mode: the model keeps only the diagonal factors (low-memory sweeps)")
     ap.add_argument("--step-fd", action="store_true",
                     help="step mode: also time the 2d+1 value-only evaluations of FD")
     args = ap.parse_args()
@@ -332,7 +335,7 @@ def main():
 
     prob = workloads.make_problem(args.workload if args.mode == "step" else WORKLOAD,
                                   **({"nt": args.nt} if args.nt else {}))
-    model = P.InlaModel(prob)
+    model = P.InlaModel(prob, low_memory=args.low_memory and args.mode == "step")
     theta = prob.theta.copy()
     stream = torch.cuda.current_stream()
     if args.mode == "step":

@@ -233,9 +233,9 @@ bta_status level_product(const Gemm& g, const ProdCfg& c, cudaStream_t s) {
 // a fraction (leaf / n)^2 of the b^3 / 3 + b^3 / 3 flops of the factor and
 // the inverse; the rest are the four products of each level.
 bta_status rec_hybrid(const PB& b, int64_t aoff, int n, int ld, int64_t woff, int soff,
-                      int leaf, const ProdCfg& pc, cudaStream_t s) {
+                      int leaf, const ProdCfg& pc, cudaStream_t s, bool top = false) {
   const int cnt = b.cnt;
-  if (n <= leaf) {
+  if (n <= leaf && !top) {
     double* A[kMaxBatch];
     double* W[kMaxBatch];
     double* sl[kMaxBatch];
@@ -313,15 +313,26 @@ int env_int(const char* name, int dflt) {
 }  // namespace
 
 int potrf_hybrid_leaf(int precision) {
-  // Largest block the task-graph kernel factors whole (0: always whole).
-  // Up to 1024 rows its serial chain of 32-row pivots costs about as much
-  // as the split's extra launches; above, the split wins (measured on GB300:
-  // b = 2025 1.6x (emulated) and 1.9x (mixed) faster per gradient, b = 4800
-  // 2.2x; FP64 b = 2025 1.4 %).
+  // Largest block the task-graph kernel factors whole below the top level
+  // (0: always whole).  Up to 1024 rows its serial chain of 32-row pivots
+  // costs about as much as the split's extra products; above, the split wins
+  // (measured on GB300: b = 2025 1.6x (emulated) and 1.9x (mixed) faster per
+  // gradient, b = 4800 2.2x; FP64 b = 2025 1.4 %).
   static const int fp64 = env_int("BTA_POTRF_LEAF_FP64", 1024);
   static const int tc = env_int("BTA_POTRF_LEAF_TC", 1024);
   return precision == 0 ? fp64 : tc;
 }
+
+namespace {
+// Blocks above this many rows are split at least once (tensor-core modes):
+// with the emulated products a 1024-row block is faster as two 512-row
+// task graphs (GB300: 157 -> 154 ms emulated, 142 -> 130 ms mixed per
+// gradient of the b = 1024 model), while deeper splits of larger blocks lose.
+int potrf_hybrid_top(int precision) {
+  static const int tc = env_int("BTA_POTRF_SPLIT_TC", 512);
+  return precision == 0 ? 0 : tc;
+}
+}  // namespace
 
 bta_status potrf_inv_batch_prec(int count, double* const* A, int n, int ld,
                                 double* const* scratch, double* const* logdet_parts,
@@ -329,9 +340,11 @@ bta_status potrf_inv_batch_prec(int count, double* const* A, int n, int ld,
                                 void* const* tcws, int32_t* const* tcstat, cudaStream_t s) {
   if (n <= 0 || n % T || count < 0) return BTA_ERR_ARG;
   const int leaf = potrf_hybrid_leaf(precision);
+  int top = potrf_hybrid_top(precision);
+  if (top <= 0 || top > leaf) top = leaf;   // the top-level split threshold
   bool tc_ok = precision == 0 || (tcws && tcstat && n <= 5120);
   for (int z = 0; tc_ok && precision != 0 && z < count; ++z) tc_ok = tcws[z] && tcstat[z];
-  if (leaf < T || n <= leaf || !tc_ok || n / T > 160 || g_potrf_recursive)
+  if (leaf < T || top < T || n <= top || n < 2 * T || !tc_ok || n / T > 160 || g_potrf_recursive)
     return potrf_inv_batch(count, A, n, ld, scratch, logdet_parts, fail, fail_code, s);
   PriorityScope prio(highest_priority());
   ProdCfg pc;
@@ -348,7 +361,7 @@ bta_status potrf_inv_batch_prec(int count, double* const* A, int n, int ld,
     }
     pc.tcws = tcws ? tcws + z0 : nullptr;
     pc.tcstat = tcstat ? tcstat + z0 : nullptr;
-    BTA_TRY(rec_hybrid(b, 0, n, ld, 0, 0, (leaf / T) * T, pc, s));
+    BTA_TRY(rec_hybrid(b, 0, n, ld, 0, 0, (leaf / T) * T, pc, s, /*top=*/true));
   }
   return BTA_OK;
 }
