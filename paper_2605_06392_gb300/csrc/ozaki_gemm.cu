@@ -518,7 +518,7 @@ __device__ __forceinline__ int bar_or_512(int v) {
 }
 
 struct OzqArgs {
-  int Mp, Np, Bp, nk, nchunks, splits;   // Bp: rows per B slice in its array
+  int Mp, Np, Bp, nk, splits;   // nk: 32-wide K slabs; Bp: rows per B slice in its array
   int group;                             // tile rows per group of the launch order
   int out_lower;
   long long* partial;   // [splits][Np][Mp] integer sums, units 2^-35 of level 2
@@ -566,8 +566,11 @@ __global__ void __launch_bounds__(kQThreads, 1)
   const int in = (int)blockIdx.x - grp * g.group * nt_all;
   const int m0 = (grp * g.group + in % gm) * OM, n0 = (in / gm) * QN, z = blockIdx.z;
   if (g.out_lower && n0 > m0 + OM - 1) return;   // whole CTA exits before any set-up
-  const int c0 = (int)((int64_t)z * g.nchunks / g.splits);
-  const int c1 = (int)((int64_t)(z + 1) * g.nchunks / g.splits);
+  // this CTA's slabs of K: split z of `splits` near-equal ranges, taken in
+  // chunks of at most 16 slabs (512 of K: the exactness limit of a level sum)
+  const int ks0 = (int)((int64_t)z * g.nk / g.splits);
+  const int ks1 = (int)((int64_t)(z + 1) * g.nk / g.splits);
+  const int nc = (ks1 - ks0 + kChunkSlabs - 1) / kChunkSlabs;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -609,8 +612,8 @@ __global__ void __launch_bounds__(kQThreads, 1)
     const uint32_t leader = lane == 0;
     int r = 0;
     bool stop = false;
-    for (int c = c0; c < c1 && !stop; ++c) {
-      const int kt0 = c * kChunkSlabs, kt1 = min(g.nk, kt0 + kChunkSlabs);
+    for (int c = 0; c < nc && !stop; ++c) {
+      const int kt0 = ks0 + c * kChunkSlabs, kt1 = min(ks1, kt0 + kChunkSlabs);
       for (int P = 0; P < kQPasses && !stop; ++P) {
         const int aj0 = q_a0(P), bl0 = q_b0(P);
         for (int kt = kt0; kt < kt1; ++kt, ++r) {
@@ -646,8 +649,8 @@ __global__ void __launch_bounds__(kQThreads, 1)
     const uint64_t dbase = sdesc64(smem_u32(smem));
     bool stop = false;
     int r = 0, e = 0;   // slabs consumed, accumulator sets handed to the drain
-    for (int c = c0; c < c1 && !stop; ++c) {
-      const int kt0 = c * kChunkSlabs, kt1 = min(g.nk, kt0 + kChunkSlabs);
+    for (int c = 0; c < nc && !stop; ++c) {
+      const int kt0 = ks0 + c * kChunkSlabs, kt1 = min(ks1, kt0 + kChunkSlabs);
       for (int P = 0; P < kQPasses && !stop; ++P) {
         // P0 and P1 open an accumulator set: wait until the previous one is drained
         if (P <= 1 && e > 0 &&
@@ -694,7 +697,7 @@ __global__ void __launch_bounds__(kQThreads, 1)
 #pragma unroll
     for (int q = 0; q < 32; ++q) acc[q] = 0ll;
     int failed = 0, e = 0;
-    for (int c = c0; c < c1 && !failed; ++c) {
+    for (int c = 0; c < nc && !failed; ++c) {
       for (int set = 0; set < 2; ++set, ++e) {
         const bool ok = mbar_wait(smem_u32(&bars[kAccFull]), (uint32_t)(e & 1), kOzWaitLimit);
         if (bar_or_512(!ok || *(volatile int*)&s_abort)) {
@@ -952,16 +955,18 @@ bta_status make_map_bf16(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap* map
 }
 
 // Which kernel a product takes: 128 x 64 tiles, or (S = 8) 128 x 128 tiles
-// with the K chunks split over `splits` CTAs per tile.  A wave model: the
-// CTA of either kernel takes about as long per 512 of K, so the time goes
-// as (waves of CTAs) x (chunks per CTA); the 128 x 128 kernel is taken
-// when that is smaller (BTA_OZAKI_N128 = 0 / 1 forces the choice).
+// with the K slabs split over `splits` CTAs per tile.  A wave model in units
+// of one slab's MMAs (about the same time in either kernel) plus a fixed cost
+// of ~4 slabs a CTA (set-up, drains, store): the time goes as (waves of CTAs)
+// x (slabs per CTA + 4); the 128 x 128 kernel is taken when that is smaller
+// (BTA_OZAKI_N128 = 0 / 1 forces the choice).
 struct OzPlan {
   bool n128 = false;
   int splits = 1;
 };
 constexpr int kSmCount = 152;
-constexpr int kMaxSplits = 8;
+constexpr int kMaxSplits = 16;
+constexpr int kCtaFixedSlabs = 4;
 
 OzPlan oz_plan(int M, int N, int K, int S) {
   static const int force = [] {
@@ -970,14 +975,14 @@ OzPlan oz_plan(int M, int N, int K, int S) {
   }();
   OzPlan p;
   if (S != 8 || force == 0) return p;
-  const int64_t nch = cdiv(cdiv(K, OK16), kChunkSlabs);
+  const int64_t nk = cdiv(K, OK16);
   const int64_t t64 = (int64_t)cdiv(M, OM) * cdiv(N, OBN);
   const int64_t t128 = (int64_t)cdiv(M, OM) * cdiv(N, QN);
-  const int64_t est64 = cdiv(t64, kSmCount) * nch;
+  const int64_t est64 = cdiv(t64, kSmCount) * (nk + kCtaFixedSlabs);
   int64_t best = -1;
-  for (int sp = 1; sp <= kMaxSplits && sp <= nch; ++sp) {
+  for (int sp = 1; sp <= kMaxSplits && sp <= nk; ++sp) {
     if (sp > 1 && t128 * sp > kSmCount) break;   // keeps the split sums small
-    const int64_t est = cdiv(t128 * sp, kSmCount) * cdiv(nch, sp);
+    const int64_t est = cdiv(t128 * sp, kSmCount) * (cdiv(nk, sp) + kCtaFixedSlabs);
     if (best < 0 || est < best) {
       best = est;
       p.splits = sp;
@@ -1052,7 +1057,6 @@ bta_status launch_ozaki(const Gemm& g, uint8_t* ws, int32_t* status, cudaStream_
     OzqArgs q;
     q.Mp = L.Mp; q.Np = L.Np; q.Bp = bpitch;
     q.nk = L.Kp / OK16;
-    q.nchunks = cdiv(q.nk, kChunkSlabs);
     q.splits = plan.splits;
     q.out_lower = g.out_lower;
     q.partial = partial;
