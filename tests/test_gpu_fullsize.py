@@ -65,7 +65,7 @@ def test_benchmark_model_full_size(P):
     m.close()
 
 
-def test_large_ragged_model_fp64_and_mixed(P):
+def test_large_ragged_model_all_precisions(P):
     prob = workloads.make_problem("st_large")
     m = P.InlaModel(prob)
     assert m.ld == 2048 and m.b == 2025
@@ -86,6 +86,17 @@ def test_large_ragged_model_fp64_and_mixed(P):
     assert np.max(np.abs(xm - x)) <= 1e-8 * np.max(np.abs(x))
     assert _residual(prob, xm) < 1e-10
     np.testing.assert_allclose(pm["phase_c"], pc, rtol=1e-5, atol=1e-3)
+    # emulated FP64 (split diagonal factor: 2048 -> 1024-row task graphs with
+    # emulated level products): the FP64 bar against the closed forms and the
+    # FP64 path
+    fe, ge = m.value_and_grad(prob.theta, precision=2)
+    pe = m.last_parts()
+    xe = m.mode().cpu().numpy()
+    assert abs(pe["logdet_p"] - ld) <= 1e-10 * abs(ld)
+    np.testing.assert_allclose(pe["phase_c"], pc, rtol=1e-10, atol=1e-8)
+    assert abs(fe - f) <= 1e-10 * abs(f)
+    assert np.max(np.abs(ge - g) / scale) <= 1e-10
+    assert np.max(np.abs(xe - x)) <= 1e-10 * np.max(np.abs(x))
     m.close()
 
 

@@ -279,7 +279,7 @@ def test_multi_tile_block_1024(P, name):
     assert np.max(np.abs(g - o.grad) / _grad_scale(o)) <= RTOL
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_multi_model_single_graph_batch(P, precision):
     # models of uneven block size (b = 64, 120, 48 -> ld 64, 128, 64) in one graph
     probs = [workloads.make_problem("st_tiny"),
@@ -295,7 +295,7 @@ def test_multi_model_single_graph_batch(P, precision):
             np.testing.assert_array_equal(g[i], singles[i][1])
     fv, _ = batch.value_and_grad([p.theta for p in probs], grad=False, precision=precision)
     np.testing.assert_array_equal(fv, f)
-    if precision == 0:
+    if precision != 1:   # FP64 and emulated FP64 meet the FP64 bar
         for i, p in enumerate(probs):
             o = _oracle(p)
             assert abs(f[i] - o.f) <= RTOL * abs(o.f)
