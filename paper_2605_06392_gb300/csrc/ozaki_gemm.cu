@@ -480,29 +480,37 @@ __device__ __forceinline__ void q_pair(uint32_t tmem, uint64_t dst, uint32_t fir
   }
 }
 
-template <int P, int I, int LL, int KK>
-__device__ __forceinline__ void q_row(uint32_t tmem, uint64_t dst, uint32_t first,
-                                      uint32_t leader) {
-  if constexpr (LL < 4) {
-    q_pair<P, I, LL, KK>(tmem, dst, first, leader);
-    q_row<P, I, LL + 1, KK>(tmem, dst, first, leader);
+// One slab of sub-pass P in level-major order: for each level, its pairs
+// (A slot ascending) and both 16-wide K steps back to back, so consecutive
+// MMAs accumulate into the same TMEM accumulator.  A level's first MMA is
+// its pair with A slot 0 at K step 0 (present in every level of P0 and P1),
+// which opens the accumulator in the first slab of a chunk.
+template <int P, int L, int I>
+__device__ __forceinline__ void q_level(uint32_t tmem, uint64_t dst, uint32_t first,
+                                        uint32_t leader) {
+  if constexpr (I < 4) {
+    constexpr int LL = L - 2 - q_a0(P) - q_b0(P) - I;
+    if constexpr (LL >= 0 && LL < 4) {
+      q_pair<P, I, LL, 0>(tmem, dst, first, leader);
+      q_pair<P, I, LL, 1>(tmem, dst, first, leader);
+    }
+    q_level<P, L, I + 1>(tmem, dst, first, leader);
   }
 }
 
-template <int P, int I, int KK>
-__device__ __forceinline__ void q_step(uint32_t tmem, uint64_t dst, uint32_t first,
-                                       uint32_t leader) {
-  if constexpr (I < 4) {
-    q_row<P, I, 0, KK>(tmem, dst, first, leader);
-    q_step<P, I + 1, KK>(tmem, dst, first, leader);
+template <int P, int L>
+__device__ __forceinline__ void q_levels(uint32_t tmem, uint64_t dst, uint32_t first,
+                                         uint32_t leader) {
+  if constexpr (L <= 9) {
+    q_level<P, L, 0>(tmem, dst, first, leader);
+    q_levels<P, L + 1>(tmem, dst, first, leader);
   }
 }
 
 template <int P>
 __device__ __forceinline__ void q_slab(uint32_t tmem, uint64_t dst, uint32_t first,
                                        uint32_t leader) {
-  q_step<P, 0, 0>(tmem, dst, first, leader);
-  q_step<P, 0, 1>(tmem, dst, first, leader);
+  q_levels<P, 2>(tmem, dst, first, leader);
 }
 
 // OR of v over the 512 threads of warps 0-15 (named barrier 1).
@@ -666,7 +674,8 @@ __global__ void __launch_bounds__(kQThreads, 1)
             stop = true;
             break;
           }
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          // (no tcgen05 fence here: the slab arrives by TMA, whose mbarrier
+          // completion already orders it before the MMAs that read it)
           const uint64_t dst = dbase + (uint64_t)((s * kQStage) >> 4);
           const uint32_t first = kt == kt0;
           if (P == 0) q_slab<0>(tmem, dst, first, leader);
