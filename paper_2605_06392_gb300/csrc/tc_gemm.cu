@@ -66,8 +66,21 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, 
       : "memory");
 }
 
+// FP32 accumulator value widened to FP64 with integer operations (GB300's
+// FP64 pipe, conversions included, runs one warp instruction per ~64
+// cycles); zero and subnormal inputs take the conversion.
+__device__ __forceinline__ double widen(float x) {
+  const uint32_t u = __float_as_uint(x);
+  const uint32_t e = (u >> 23) & 0xFF;
+  if (e == 0 || e == 0xFF) return (double)x;
+  return __longlong_as_double((long long)(((unsigned long long)(u & 0x80000000u) << 32) |
+                                          ((unsigned long long)(e - 127 + 1023) << 52) |
+                                          ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+}
+
 struct TcArgs {
   int M, N, K;
+  int amode, bmode;   // alpha: 0 -> 1, 1 -> -1, 2 -> general; beta: 0 -> 0, 1 -> 1, 2 -> general
   double alpha, beta;
   double* C;
   int ldc;
@@ -177,8 +190,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         for (int j = 0; j < 32; ++j) {
           const int n = n0 + c + j;
           if (n >= g.N || (g.out_lower && m < n)) continue;
-          double out = g.alpha * (double)v[j];
-          if (g.beta != 0.0) out = fma(g.beta, g.Cin[m + (int64_t)n * g.ldcin], out);
+          double out = widen(v[j]);
+          if (g.amode == 1) out = -out;
+          else if (g.amode == 2) out *= g.alpha;
+          if (g.bmode == 1) out += g.Cin[m + (int64_t)n * g.ldcin];
+          else if (g.bmode == 2) out = fma(g.beta, g.Cin[m + (int64_t)n * g.ldcin], out);
           g.C[m + (int64_t)n * g.ldc] = out;
         }
       }
@@ -195,6 +211,57 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
 // Y (rows x Kp, row-major fp32 hi/lo) = split(op(X)) with
 // op(X)[r][k] = trans ? X[k + r*ldx] : X[r + k*ldx], masked to its triangle.
+// v = hi + lo + O(2^-22 |v|) with hi, lo TF32 (10 stored mantissa bits):
+// hi is v rounded to nearest (ties away from zero) at its 10th mantissa bit,
+// lo = v - hi (exact, at most 42 significant bits) rounded the same way.
+// Both come from v's bit pattern with integer operations; exponents outside
+// [2^-70, 2^100] (zero included) take FP32 conversions instead.
+__device__ __forceinline__ void tf32_split(double v, float& h, float& l) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int e = (int)((b >> 52) & 0x7FF);
+  if (e < 1023 - 70 || e > 1023 + 100) {
+    uint32_t hb, lb;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"((float)v));
+    h = __uint_as_float(hb);
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lb) : "f"((float)(v - (double)h)));
+    l = __uint_as_float(lb);
+    return;
+  }
+  const unsigned long long sgn = b & (1ull << 63);
+  const unsigned long long mag = b ^ sgn;
+  const unsigned long long hmag = (mag + (1ull << 41)) & ~((1ull << 42) - 1);
+  const int he = (int)(hmag >> 52);   // e, or e + 1 when the rounding carried
+  const uint32_t s32 = (uint32_t)(sgn >> 32);
+  h = __uint_as_float(s32 | ((uint32_t)(he - 1023 + 127) << 23) |
+                      (uint32_t)((hmag >> 29) & 0x7FFFFFu));
+  // lo in units of 2^(e - 1075): significand of v minus that of hi
+  const long long vs = (long long)((mag & ((1ull << 52) - 1)) | (1ull << 52));
+  const long long hs = he == e ? (long long)((hmag & ((1ull << 52) - 1)) | (1ull << 52))
+                               : (long long)(1ull << 53);
+  const long long d = vs - hs;   // |d| <= 2^41
+  if (d == 0) {
+    l = __uint_as_float(s32);    // signed zero
+    return;
+  }
+  const unsigned long long ad = (unsigned long long)(d < 0 ? -d : d);
+  const int nb = 64 - __clzll((long long)ad);   // significant bits of |d|
+  unsigned long long q = ad;
+  int ex = 0;
+  if (nb > 11) {   // keep 11 significant bits, nearest, ties away from zero
+    const int sh = nb - 11;
+    q = (ad + (1ull << (sh - 1))) >> sh;
+    ex = sh;
+    if (q >> 11) {
+      q >>= 1;
+      ++ex;
+    }
+  }
+  const int qb = 63 - __clzll((long long)q);    // leading-one position of q
+  const int fe = qb + ex + e - 1075 + 127;        // >= 5 for e >= 1023 - 70
+  l = __uint_as_float((s32 ^ (d < 0 ? 0x80000000u : 0u)) | ((uint32_t)fe << 23) |
+                      (uint32_t)((q << (23 - qb)) & 0x7FFFFFu));
+}
+
 __global__ void split_tf32_kernel(int rows, int K, int Kp, const double* __restrict__ X, int ldx,
                                   int trans, int tri, float* __restrict__ hi,
                                   float* __restrict__ lo) {
@@ -216,12 +283,8 @@ __global__ void split_tf32_kernel(int rows, int K, int Kp, const double* __restr
   for (int yy = ty; yy < 32; yy += 8) {
     const int r = r0 + yy, k = k0 + tx;
     if (r >= rows || k >= Kp) continue;
-    const double v = t[yy][tx];
-    uint32_t hb, lb;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"((float)v));
-    const float h = __uint_as_float(hb);
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lb) : "f"((float)(v - (double)h)));
-    const float l = __uint_as_float(lb);
+    float h, l;
+    tf32_split(t[yy][tx], h, l);
     hi[(int64_t)r * Kp + k] = h;
     lo[(int64_t)r * Kp + k] = l;
   }
@@ -305,6 +368,8 @@ bta_status tc_gemm_mixed(const Gemm& g, void* ws, int32_t* status, cudaStream_t 
   }
   TcArgs a;
   a.M = M; a.N = N; a.K = K; a.alpha = g.alpha; a.beta = g.beta; a.C = g.C; a.ldc = g.ldc;
+  a.amode = g.alpha == 1.0 ? 0 : g.alpha == -1.0 ? 1 : 2;
+  a.bmode = g.beta == 0.0 ? 0 : g.beta == 1.0 ? 1 : 2;
   a.Cin = g.Cin ? g.Cin : g.C; a.ldcin = g.Cin ? g.ldcin : g.ldc; a.out_lower = g.out_lower;
   a.status = status;
   dim3 grid(cdiv(M, TM), cdiv(N, TN));
