@@ -430,9 +430,13 @@ static bta_status model_create_impl(const inla_model_spec* sp, inla_model* m) {
         traw[(size_t)v * a * a + f + (size_t)(v * a_r + i2) * a] += cv[i] * cv[i2];
     }
   }
+  // with no fixed effects (a = 0) the arrow arrays are empty: keep one zero
+  // element so that every device array exists
+  if (craw.empty()) craw.assign(1, 0.0);
+  if (traw.empty()) traw.assign(1, 0.0);
   BTA_TRY(upload(m, &md.cnt, cnt.data(), cnt.size()));
-  BTA_TRY(upload(m, &md.craw, craw.data(), std::max<size_t>(craw.size(), 1)));
-  BTA_TRY(upload(m, &md.traw, traw.data(), std::max<size_t>(traw.size(), 1)));
+  BTA_TRY(upload(m, &md.craw, craw.data(), craw.size()));
+  BTA_TRY(upload(m, &md.traw, traw.data(), traw.size()));
   BTA_TRY(upload(m, &md.rraw, rraw.data(), rraw.size()));
   BTA_TRY(upload(m, &md.obs_lat, lat.data(), lat.size()));
   BTA_TRY(upload(m, &md.obs_v, sp->n_obs ? sp->obs_v : lat.data(), lat.size()));

@@ -122,6 +122,7 @@ def _eval(P, prob, precision):
     ("coreg_tiny", {}),
     ("coreg_small", {}),
     ("st_tiny", dict(nx=16, ny=12, nt=3, n_obs=700)),
+    ("st_tiny", dict(a=0)),
     ("st_medium_nt6", {}),
 ])
 def test_emulated_mode_meets_fp64_bar(P, name, over):

@@ -40,6 +40,7 @@ CASES = [
     ("st_tiny", dict(nx=10, ny=9, nt=5, n_obs=900)),              # b=90 -> ld=96, ragged
     ("st_tiny", dict(nx=16, ny=12, nt=3, n_obs=700)),             # b=192: 6 tiles, odd split
     ("st_tiny", dict(nt=1, n_obs=100)),                           # a single time block
+    ("st_tiny", dict(a=0)),                                       # no fixed effects: no arrow
     ("coreg_tiny", {}),                                           # k=3, b=48 -> 64
     ("coreg_k2_small", {}),                                       # k=2, b=60 -> 64
     ("coreg_small", dict(nt=3, n_obs=1200)),                      # k=3, b=192

@@ -148,18 +148,20 @@ def test_selinv_identities_from_selected_blocks_only():
     np.testing.assert_allclose(accT, np.eye(a), atol=1e-10)
 
 
-@pytest.mark.parametrize("name", ["st_tiny", "coreg_tiny"])
-def test_gradient_matches_central_fd(name):
-    p = workloads.make_problem(name)
+@pytest.mark.parametrize("name,over", [("st_tiny", {}), ("coreg_tiny", {}),
+                                       ("st_tiny", {"a": 0})])   # no fixed effects: no arrow
+def test_gradient_matches_central_fd(name, over):
+    p = workloads.make_problem(name, **over)
     g = dense.evaluate(p).grad
     gfd = oracle.fd.gradient(p, h=1e-5, path="dense")
     scale = np.maximum(np.abs(g), 1.0)
     assert np.max(np.abs(g - gfd) / scale) < 1e-7
 
 
-@pytest.mark.parametrize("name", ["st_tiny", "coreg_tiny"])
-def test_bta_path_equals_dense_path(name):
-    p = workloads.make_problem(name)
+@pytest.mark.parametrize("name,over", [("st_tiny", {}), ("coreg_tiny", {}),
+                                       ("st_tiny", {"a": 0})])
+def test_bta_path_equals_dense_path(name, over):
+    p = workloads.make_problem(name, **over)
     d = dense.evaluate(p)
     b = bta.evaluate(p)
     assert abs(d.f - b.f) <= 1e-12 * abs(d.f)
