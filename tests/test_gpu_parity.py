@@ -41,6 +41,10 @@ CASES = [
     ("st_tiny", dict(nx=16, ny=12, nt=3, n_obs=700)),             # b=192: 6 tiles, odd split
     ("st_tiny", dict(nt=1, n_obs=100)),                           # a single time block
     ("st_tiny", dict(a=0)),                                       # no fixed effects: no arrow
+    ("st_tiny", dict(n_obs=0)),                                   # no observations: Q_c = Q_p
+    ("st_tiny", dict(nx=1, ny=1)),                                # b = 1 padded to 32
+    ("st_tiny", dict(nx=3, ny=1, nt=2, n_obs=30)),                # a 1-D grid, b = 3
+    ("coreg_tiny", dict(n_obs=0)),
     ("coreg_tiny", {}),                                           # k=3, b=48 -> 64
     ("coreg_k2_small", {}),                                       # k=2, b=60 -> 64
     ("coreg_small", dict(nt=3, n_obs=1200)),                      # k=3, b=192

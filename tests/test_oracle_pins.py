@@ -159,7 +159,9 @@ def test_gradient_matches_central_fd(name, over):
 
 
 @pytest.mark.parametrize("name,over", [("st_tiny", {}), ("coreg_tiny", {}),
-                                       ("st_tiny", {"a": 0})])
+                                       ("st_tiny", {"a": 0}), ("st_tiny", {"n_obs": 0}),
+                                       ("st_tiny", {"nx": 1, "ny": 1}),
+                                       ("st_tiny", {"nx": 3, "ny": 1, "nt": 2, "n_obs": 30})])
 def test_bta_path_equals_dense_path(name, over):
     p = workloads.make_problem(name, **over)
     d = dense.evaluate(p)
