@@ -100,6 +100,24 @@ def test_large_ragged_model_all_precisions(P):
     m.close()
 
 
+def test_blocks_above_task_graph_limit(P):
+    """b = 5184 (72 x 72 grid, two time blocks): past the task graph's 160
+    tile rows the diagonal factor takes the recursive launch sequence, and
+    past K = 5120 the emulated products fall back to FP64.  Every mode
+    against the oracle at its own bar."""
+    from oracle import bta
+    prob = workloads.make_problem("st_tiny", nx=72, ny=72, nt=2, n_obs=3000)
+    o = bta.evaluate(prob)
+    scale = np.maximum(np.abs(o.grad), np.abs(o.phase_a) + np.abs(o.phase_b) + np.abs(o.phase_c))
+    m = P.InlaModel(prob)
+    assert m.ld == 5184
+    for prec, (tf, tg) in ((0, (1e-10, 1e-10)), (1, (1e-6, 1e-4)), (2, (1e-10, 1e-10))):
+        f, g = m.value_and_grad(prob.theta, precision=prec)
+        assert abs(f - o.f) <= tf * abs(o.f), (prec, f, o.f)
+        assert np.max(np.abs(g - o.grad) / scale) <= tg, prec
+    m.close()
+
+
 def test_production_model_emulated_low_memory(P):
     """Three coregionalised responses on a 40 x 40 grid, b = 4800, 192 time
     blocks, a = 12, d = 15, 2e6 observations, in the emulated-FP64 mode with
