@@ -68,3 +68,61 @@ def test_grid_stencil_host_only():
 def test_build_is_sm103a_only():
     from paper_2605_06392_gb300 import build
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def _valid_spec_arrays():
+    import paper_2605_06392_gb300 as P
+    row_ptr, col, vC, vG, vGG = P.grid_stencil(3, 2)
+    keep = dict(row_ptr=row_ptr, col=col, vC=vC, vG=vG, vGG=vGG,
+                mdiag=np.ones(6), msub=np.zeros(5), t=np.zeros(4, np.int32),
+                s=np.arange(4, dtype=np.int32), v=np.zeros(4, np.int32), cov=np.zeros(8),
+                y=np.ones(4))
+    return keep
+
+
+def _spec(keep, **over):
+    import ctypes as C
+    from paper_2605_06392_gb300 import _capi
+
+    def ptr(a):
+        return a.ctypes.data_as(C.c_void_p)
+    f = dict(k=1, ns=6, nt=2, a=2, nnz=int(keep["col"].shape[0]), row_ptr=ptr(keep["row_ptr"]),
+             col=ptr(keep["col"]), val_C=ptr(keep["vC"]), val_G=ptr(keep["vG"]),
+             val_GG=ptr(keep["vGG"]), m_diag=ptr(keep["mdiag"]), m_sub=ptr(keep["msub"]),
+             n_obs=4, obs_t=ptr(keep["t"]), obs_s=ptr(keep["s"]), obs_v=ptr(keep["v"]),
+             obs_cov=ptr(keep["cov"]), y=ptr(keep["y"]), tip_prior=1e-3, theta_prior_var=100.0,
+             low_memory=0)
+    f.update(over)
+    return _capi.inla_model_spec(**f)
+
+
+@pytest.mark.parametrize("over", [
+    dict(k=0), dict(k=5), dict(ns=0), dict(nt=0), dict(a=-1), dict(a=33),
+    dict(k=2, ns=3, a=3),               # a must split evenly over the responses
+    dict(nnz=0), dict(row_ptr=None), dict(m_sub=None), dict(n_obs=-1),
+    dict(obs_cov=None), dict(y=None),
+])
+def test_model_spec_rejected_before_any_device_work(lib, over):
+    """Invalid specs return BTA_ERR_ARG from the host checks, which run before
+    the first device allocation (so this needs no GPU)."""
+    import ctypes as C
+    keep = _valid_spec_arrays()
+    h = C.c_void_p()
+    assert lib.inla_model_create(C.byref(_spec(keep, **over)), C.byref(h)) == -1
+    assert not h.value
+
+
+def test_model_spec_pattern_checks(lib):
+    import ctypes as C
+    keep = _valid_spec_arrays()
+    h = C.c_void_p()
+    bad = keep["col"].copy()
+    bad[0] = 99                          # column outside the grid
+    keep2 = dict(keep, col=bad)
+    assert lib.inla_model_create(C.byref(_spec(keep2)), C.byref(h)) == -1
+    nodiag = keep["col"].copy()
+    r0, r1 = keep["row_ptr"][0], keep["row_ptr"][1]
+    nodiag[r0:r1] = np.where(nodiag[r0:r1] == 0, 1, nodiag[r0:r1])   # row 0 loses its diagonal
+    keep3 = dict(keep, col=nodiag)
+    assert lib.inla_model_create(C.byref(_spec(keep3)), C.byref(h)) == -1
+    assert lib.inla_model_create(None, C.byref(h)) == -1
