@@ -208,3 +208,20 @@ def test_both_kernels_within_bound(P, force):
 
 if __name__ == "__main__":
     _child_gemm()
+
+
+@pytest.mark.parametrize("precision", [2, 1])
+def test_concurrent_thetas_equal_single_calls(P, precision):
+    """Three thetas evaluated as one concurrent group (every block step one
+    launch over the three matrices, the 1024-row diagonal blocks split over
+    512-row task graphs with per-matrix level products) give the bits of
+    three single evaluations."""
+    prob = workloads.make_problem("st_medium_nt6")
+    m = P.InlaModel(prob)
+    thetas = np.array([prob.theta, prob.theta + 0.05, prob.theta - 0.05])
+    singles = [m.value_and_grad(t, precision=precision) for t in thetas]
+    f, g = m.value_and_grad(thetas, concurrent=3, precision=precision)
+    for i in range(3):
+        assert f[i] == singles[i][0]
+        np.testing.assert_array_equal(g[i], singles[i][1])
+    m.close()
