@@ -117,10 +117,15 @@ typedef struct {
                           and the selected-inversion products in split TF32
                           on the tensor cores (FP32 accumulation); diagonal
                           block factorisation, log-determinants, arrow and tip
-                          in FP64; one FP64 refinement step on x*.
+                          in FP64 (diagonal blocks above 512 rows are split
+                          2 x 2, their inner products emulated to FP64
+                          accuracy as in mode 2); one FP64 refinement step on
+                          x*.
                           2: emulated FP64 -- the same b x b products as in
-                          mode 1 computed to FP64 accuracy on the BF16 tensor
-                          cores (8 slices, as bta_gemm_emulated; b <= 5120),
+                          mode 1, and the inner products of split diagonal
+                          blocks, computed to FP64 accuracy on the BF16 tensor
+                          cores (8 slices, as bta_gemm_emulated; products with
+                          K > 5120 fall back to FP64); the arrow products and
                           everything else as in mode 0                        */
   int32_t use_graph;   /* 1: capture the evaluation in a CUDA graph, replay */
   int32_t streams;     /* thetas evaluated together for batch > 1 (1..16): their
