@@ -126,3 +126,25 @@ def test_model_spec_pattern_checks(lib):
     keep3 = dict(keep, col=nodiag)
     assert lib.inla_model_create(C.byref(_spec(keep3)), C.byref(h)) == -1
     assert lib.inla_model_create(None, C.byref(h)) == -1
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without the compiled library the binding raises; there is no other
+    compute path to fall back to."""
+    from paper_2605_06392_gb300 import _capi
+    monkeypatch.setattr(_capi, "_lib", None)
+    monkeypatch.setattr(_capi, "LIB_PATH", str(tmp_path / "absent" / "libbta.so"))
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        _capi.lib()
+
+
+def test_package_imports_without_touching_the_gpu():
+    import subprocess
+    import sys
+    code = ("import sys, torch; import paper_2605_06392_gb300 as P; "
+            "import paper_2605_06392_gb300.optimize; "
+            "assert not torch.cuda.is_initialized(); "
+            "assert 'oracle' not in sys.modules; print('ok')")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stderr[-2000:]
