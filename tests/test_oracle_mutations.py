@@ -95,3 +95,45 @@ def test_model_blocks_match_neighbour_loop_construction():
         np.testing.assert_allclose(blk.D[t], D, rtol=1e-13, atol=1e-12)
     for t in range(p.nt - 1):
         np.testing.assert_allclose(blk.B[t], B, rtol=1e-13, atol=1e-12)
+
+
+def test_likelihood_normalisation_error_is_caught(monkeypatch):
+    # n log tau in place of (n/2) log tau in log l (Eq. 1): the value and the
+    # explicit gradient term both move, and both pins on log l see it
+    from test_oracle_likelihood_pins import closed_form_gaps, loglik_density_gap, scalar_problem
+
+    def doubled(model, x):
+        val, grad = orig(model, x)
+        prob, k = model.prob, model.prob.k
+        for m in range(k):
+            nm = int(np.sum(prob.obs_v == m))
+            val += 0.5 * nm * np.log(model.par.tau[m])
+            grad[grad.shape[0] - k + m] += 0.5 * nm
+        return val, grad
+    orig = M.log_lik
+    monkeypatch.setattr(M, "log_lik", doubled)
+    p = workloads.make_problem("coreg_tiny")
+    gap, gerr = loglik_density_gap(p, np.zeros(p.N))
+    assert gap > 1e-3 and gerr > 1e-3
+    worst_val, worst_grad = closed_form_gaps(scalar_problem(1))
+    assert worst_val > 1e-3 and worst_grad > 1e-3
+
+
+def test_fixed_effect_column_offset_is_caught(monkeypatch):
+    # the covariates of response v written into response (v + 1) mod k's
+    # fixed-effect columns: the hand-typed projection pin fails
+    from test_oracle_likelihood_pins import projection_gaps, two_response_problem
+    import scipy.sparse as sp
+
+    def shifted(prob):
+        A = orig(prob).tolil()
+        nb, ar, k = prob.nt * prob.b, prob.a_r, prob.k
+        for j in range(prob.n_obs):
+            v = int(prob.obs_v[j])
+            for c in range(ar):
+                A[j, nb + v * ar + c] = 0.0
+                A[j, nb + ((v + 1) % k) * ar + c] = prob.obs_cov[j, c]
+        return sp.csr_matrix(A)
+    orig = M.projection
+    monkeypatch.setattr(M, "projection", shifted)
+    assert projection_gaps(two_response_problem()) > 0.1
