@@ -158,14 +158,25 @@ bta_status bta_assemble(inla_model* m, const double* theta, int32_t which,
                         bta_desc* out, double* rhs, cudaStream_t stream);
 
 /*
- * bta_factor -- Algorithm 1: block Cholesky of an ASSEMBLED BTA matrix, in
- * place, fused with the lower solve L z = r when rhs_inout != NULL (device,
- * n*ld + a; overwritten by z).  logdet (device scalar) receives
- * log|Q| = 2 sum log diag(L).  fail_block (device int32) receives -1, or the
- * index of the first diagonal block (n for the tip) whose pivot was not
- * positive; in that case the factor is not usable.  The call does not
- * synchronise, so it cannot itself return BTA_ERR_NOT_SPD: read fail_block.
- * precision must be 0.  Sets state FACTORED.
+ * bta_factor -- Algorithm 1 (Section III-A): block Cholesky of an ASSEMBLED
+ * BTA matrix, in place, fused with the lower solve L z = r when rhs_inout !=
+ * NULL (device, n*ld + a; overwritten by z).  logdet (device scalar)
+ * receives log|Q| = 2 sum log diag(L).  fail_block (device int32) receives
+ *   -1               the factor is complete,
+ *   i >= 0           the index of the first diagonal block (n for the tip)
+ *                    whose pivot was not positive,
+ *   BTA_ERR_TIMEOUT  (-5) a bounded device wait of the factor expired;
+ * in both failure cases the factor is not usable.  The call does not
+ * synchronise, so it cannot itself return BTA_ERR_NOT_SPD or
+ * BTA_ERR_TIMEOUT: read fail_block.
+ * precision: as inla_opts.precision.  0: FP64.  1: mixed -- the b x b
+ * Schur-complement products (D_i -= L_B L_B^T, L_B = B L_D^{-T}) in split TF32
+ * on the tensor cores, the diagonal factors, log-determinant, arrow and tip
+ * in FP64 (relative error ~1e-9 in log|Q|, ~1e-6 in the factor; refine the
+ * solve with bta_solve(refine = 1)).  2: emulated FP64 -- the same products
+ * to FP64 accuracy on the BF16 tensor cores.  Modes 1 and 2 allocate their
+ * operand copies with cudaMallocAsync on the stream, as the workspace of
+ * every mode.  Sets state FACTORED.
  */
 bta_status bta_factor(bta_desc* q, double* rhs_inout, double* logdet, int32_t* fail_block,
                       int32_t precision, cudaStream_t stream);
@@ -177,15 +188,19 @@ bta_status bta_factor(bta_desc* q, double* rhs_inout, double* logdet, int32_t* f
  * own allocator or a fixed memory budget, a framework that forbids allocation
  * on its hot path, or code that cannot take the device-wide synchronisation a
  * free may imply.  The paper has no counterpart; this is a library-level
- * variant.  Its temporary blocks come from a fixed array the library reserves
- * on each device that loads it (2.4 MB, held until the process exits), so:
+ * variant.  Its temporary blocks come from a fixed array in the library's
+ * device memory (2.4 MB per device, held until the process exits), so:
  *   - sizes are limited to ld <= 256, a <= 32 and n * (ld / 32) + 1 <= 16384;
  *     beyond that it returns BTA_ERR_ARG without doing any work;
  *   - all calls on a device share the array: calls that overlap on the GPU
  *     race and give wrong results, so order them on one stream;
- *   - the first call on a device looks up the array's device address and
- *     caches it; make that first call before any stream capture.
- * It calls no cudaMalloc, cudaFree or allocating library routine.
+ *   - under CUDA's lazy module loading the array is reserved on a device by
+ *     the first call there (which loads the library's device code for it, and
+ *     may allocate and synchronise): make one call at set-up time, before any
+ *     stream capture.  Every call looks the array's address up again, so a
+ *     device reset leaves no stale address.
+ * Apart from that first reservation it calls no cudaMalloc, cudaFree or
+ * allocating library routine.
  */
 bta_status bta_factor_noalloc(bta_desc* q, double* rhs_inout, double* logdet,
                               int32_t* fail_block, cudaStream_t stream);
@@ -193,8 +208,15 @@ bta_status bta_factor_noalloc(bta_desc* q, double* rhs_inout, double* logdet,
 /*
  * bta_solve -- Eqs. 3-5: given a FACTORED descriptor and z (device, from the
  * fused lower solve), overwrite z by x = Q^{-1} r.  With lower = 1 the lower
- * solve L z = r is done first (so z_inout may hold r).  refine must be 0 in
- * this build (reserved for refinement against Q_or_null).
+ * solve L z = r is done first (so z_inout may hold r).
+ * refine = 1 adds one step of iterative refinement in FP64, x += L^{-T} L^{-1}
+ * (r - Q x), the step the mixed-precision mode applies to x*: it needs
+ * lower = 1 (z_inout holds r on entry) and Q_or_null, a separate ASSEMBLED
+ * descriptor of the same matrix (same n, b, a, ld; D and T lower triangles
+ * referenced), which is read, not changed.  refine = 0 ignores Q_or_null.
+ * Errors: BTA_ERR_ARG (refine without lower or Q, shape mismatch),
+ * BTA_ERR_STATE (L not FACTORED, Q not ASSEMBLED).  Allocates its workspace
+ * with cudaMallocAsync on the stream.
  */
 bta_status bta_solve(const bta_desc* L, double* z_inout, int32_t lower, int32_t refine,
                      const bta_desc* Q_or_null, cudaStream_t stream);
@@ -214,7 +236,9 @@ bta_status bta_selinv(bta_desc* L, inla_model* m, const double* theta, int32_t w
  * inla_value_and_grad -- Eq. 1 and Eq. 6.  theta: host, batch x d.  f: host,
  * batch values.  grad: host, batch x d, or NULL for the value-only path
  * (the finite-difference baseline's evaluation).  opts may be NULL.
- * Synchronises stream.  Returns BTA_ERR_NOT_SPD if a factor failed.
+ * Synchronises stream.  Returns BTA_ERR_NOT_SPD if a factor met a
+ * non-positive pivot and BTA_ERR_TIMEOUT if a bounded device wait expired
+ * (f and grad are then not usable; the model stays usable).
  * log l omits the -(n/2) log 2 pi constant and const = 0 in Eq. 1.
  */
 bta_status inla_value_and_grad(inla_model* m, const double* theta, int32_t batch, double* f,
@@ -328,6 +352,31 @@ bta_status bta_gemm_emulated(int32_t M, int32_t N, int32_t K, double alpha, cons
  */
 bta_status inla_grid_stencil(int32_t nx, int32_t ny, int32_t* nnz, int32_t* row_ptr,
                              int32_t* col, double* val_C, double* val_G, double* val_GG);
+
+/*
+ * bta_set_wait_limit -- test hook for the bounded device waits of the
+ * diagonal-block factor (the task graph of bta_factor and of every
+ * evaluation): limit_ns bounds each wait (1 ms .. 60 s; 0 restores the 2 s
+ * default); stall = 1 makes the factor's chain wait on a counter that nothing
+ * sets, so that its waits run out and the factor reports BTA_ERR_TIMEOUT
+ * (fail_block, or the status of inla_value_and_grad) without a fault.  The
+ * paper has no counterpart.  Process-wide; applies to launches recorded after
+ * the call (a CUDA graph captured before keeps its settings).  Host-only.
+ */
+bta_status bta_set_wait_limit(int64_t limit_ns, int32_t stall);
+
+/*
+ * bta_pivot_reciprocals -- the two scalar functions the diagonal-block
+ * factor applies to every pivot d (Algorithm 1's POTRF leaf), exposed so
+ * they can be checked against CUDA's own: recip_out[i] = 1 / v[i] (relative
+ * error within 2^-52 of the correctly rounded value for |v| in 2^-100 ..
+ * 2^100; the division elsewhere) and rsqrt_out[i] = v[i]^{-1/2} (within
+ * 2^-51 relative for positive v in that range; 1 / sqrt(v) elsewhere).
+ * v, recip_out, rsqrt_out: device arrays of n doubles; either output may be
+ * NULL.  Stream-ordered.  The paper has no counterpart.
+ */
+bta_status bta_pivot_reciprocals(const double* v, int64_t n, double* recip_out,
+                                 double* rsqrt_out, cudaStream_t stream);
 
 /* Number of kernels inla_value_and_grad ran for this model (CUDA-graph
  * replays counted kernel by kernel); NULL: kernels the library launched. */

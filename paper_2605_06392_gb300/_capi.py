@@ -79,6 +79,9 @@ SIGNATURES = {
     "inla_last_parts": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "inla_copy_mode": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "inla_kernel_launches": (C.c_int64, [C.c_void_p]),
+    "bta_set_wait_limit": (C.c_int, [C.c_int64, C.c_int32]),
+    "bta_pivot_reciprocals": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
+                                        C.c_void_p]),
     "bta_gemm": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_void_p, C.c_int32,
                            C.c_int32, C.c_void_p, C.c_int32, C.c_int32, C.c_double, C.c_void_p,
                            C.c_int32, C.c_void_p]),

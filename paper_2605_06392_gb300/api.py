@@ -187,19 +187,24 @@ def bta_assemble(model: InlaModel, theta, which: int, out: BtaMatrix, rhs=None, 
                              _stream(stream)), "bta_assemble")
 
 
-def bta_factor(q: BtaMatrix, rhs=None, stream=None):
-    """Returns (logdet, fail_block) as device tensors."""
+def bta_factor(q: BtaMatrix, rhs=None, precision: int = 0, stream=None):
+    """Returns (logdet, fail_block) as device tensors (fail_block: -1, the
+    first failing block, or -5 if a bounded device wait expired)."""
     logdet = torch.zeros(1, dtype=torch.float64, device="cuda")
     fail = torch.zeros(1, dtype=torch.int32, device="cuda")
     check(lib().bta_factor(C.byref(q.desc), C.c_void_p(rhs.data_ptr()) if rhs is not None else None,
-                           C.c_void_p(logdet.data_ptr()), C.c_void_p(fail.data_ptr()), 0,
-                           _stream(stream)), "bta_factor")
+                           C.c_void_p(logdet.data_ptr()), C.c_void_p(fail.data_ptr()),
+                           int(precision), _stream(stream)), "bta_factor")
     return logdet, fail
 
 
-def bta_solve(L: BtaMatrix, z, lower: bool = False, stream=None):
-    check(lib().bta_solve(C.byref(L.desc), C.c_void_p(z.data_ptr()), int(lower), 0, None,
-                          _stream(stream)), "bta_solve")
+def bta_solve(L: BtaMatrix, z, lower: bool = False, refine: bool = False,
+              Q: BtaMatrix | None = None, stream=None):
+    """z <- Q^{-1} z (lower = True: z holds r) with the factor L; refine =
+    True adds one FP64 refinement step against the assembled Q (needs lower)."""
+    check(lib().bta_solve(C.byref(L.desc), C.c_void_p(z.data_ptr()), int(lower), int(refine),
+                          C.byref(Q.desc) if Q is not None else None, _stream(stream)),
+          "bta_solve")
 
 
 def bta_selinv(L: BtaMatrix, model: InlaModel | None = None, theta=None, which: int = 1,

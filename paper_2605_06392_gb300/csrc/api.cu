@@ -263,6 +263,22 @@ bta_status record_group(inla_model* m, int mode, int cnt, int prec, cudaStream_t
   return BTA_OK;
 }
 
+// Status of one evaluation from its two failure words (parts[6], parts[7]:
+// -1, a failing block, or BTA_ERR_TIMEOUT from the task-graph factor) and the
+// tensor-core status word: a timeout outranks a non-positive pivot.
+bta_status eval_status(const double* parts, int32_t tcs) {
+  const double fc = parts[6], fp = parts[7];
+  if (tcs == BTA_ERR_TIMEOUT || fc == BTA_ERR_TIMEOUT || fp == BTA_ERR_TIMEOUT)
+    return BTA_ERR_TIMEOUT;
+  if (fc >= 0 || fp >= 0) return BTA_ERR_NOT_SPD;
+  return BTA_OK;
+}
+
+bta_status worse(bta_status a, bta_status b) {
+  if (a == BTA_ERR_TIMEOUT || b == BTA_ERR_TIMEOUT) return BTA_ERR_TIMEOUT;
+  return a != BTA_OK ? a : b;
+}
+
 // Run one group (thetas for contexts 0..cnt-1 already in htheta for mode < 2);
 // outputs land in hout[e * out_size(d)].
 bta_status run_group(inla_model* m, int mode, int cnt, int prec, int use_graph,
@@ -317,16 +333,11 @@ bta_status run_group(inla_model* m, int mode, int cnt, int prec, int use_graph,
                                  cudaMemcpyDeviceToHost, stream));
   BTA_CUDA_TRY(cudaStreamSynchronize(stream));
   bta_status st = BTA_OK;
-  if (prec) {
-    for (int e = 0; e < cnt; ++e) {
-      int32_t tcs = 0;
-      BTA_CUDA_TRY(cudaMemcpy(&tcs, m->ctx[e].fail + 2, sizeof(int32_t), cudaMemcpyDeviceToHost));
-      if (tcs != 0) st = BTA_ERR_TIMEOUT;
-    }
-  }
   for (int e = 0; e < cnt; ++e) {
+    int32_t tcs = 0;   // the tensor-core kernels' status word
+    BTA_CUDA_TRY(cudaMemcpy(&tcs, m->ctx[e].fail + 2, sizeof(int32_t), cudaMemcpyDeviceToHost));
     const double* parts = m->hout + (size_t)e * no + 1 + d;
-    if (parts[6] >= 0 || parts[7] >= 0) st = BTA_ERR_NOT_SPD;
+    st = worse(st, eval_status(parts, tcs));
     m->ctx[e].have_factors = mode == 0 ? 1 + prec : 0;   // remembers the factor's precision
   }
   m->last.assign(m->hout + (size_t)(cnt - 1) * no, m->hout + (size_t)cnt * no);
@@ -518,17 +529,29 @@ bta_status bta_assemble(inla_model* m, const double* theta, int32_t which, bta_d
 
 bta_status bta_factor(bta_desc* q, double* rhs_inout, double* logdet, int32_t* fail_block,
                       int32_t precision, cudaStream_t stream) {
-  if (!desc_ok(q, 0) || !logdet || !fail_block || precision != 0) return BTA_ERR_ARG;
+  if (!desc_ok(q, 0) || !logdet || !fail_block || precision < 0 || precision > 2)
+    return BTA_ERR_ARG;
   if (q->state != BTA_STATE_ASSEMBLED) return BTA_ERR_STATE;
   const int nsl = logdet_slots(q->n, q->ld);
-  size_t wsb = SweepWs::bytes(q->ld, q->a);
-  double* buf = nullptr;
-  BTA_CUDA_TRY(cudaMallocAsync(&buf, wsb + nsl * sizeof(double), stream));
+  const size_t wsb = SweepWs::bytes(q->ld, q->a);
+  const int ld = q->ld;
+  // tensor-core modes: operand copies of the b x b products (split TF32
+  // planes or BF16 slices, whichever is larger), 256-byte aligned
+  const size_t tcb = precision ? std::max(tc_gemm_ws_bytes(ld, ld, ld),
+                                          ld <= 5120 ? ozaki_ws_bytes(ld, ld, ld, 8) : (size_t)0)
+                               : 0;
+  const size_t head = (wsb + nsl * sizeof(double) + 255) / 256 * 256;
+  uint8_t* buf = nullptr;
+  BTA_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&buf), head + tcb, stream));
   SweepWs ws;
-  ws.carve(buf, q->ld, q->a);
-  double* slots = buf + wsb / sizeof(double);
+  ws.carve(reinterpret_cast<double*>(buf), ld, q->a);
+  double* slots = reinterpret_cast<double*>(buf) + wsb / sizeof(double);
+  if (precision) {
+    ws.tc = buf + head;
+    ws.tcstat = fail_block;   // a tensor-core timeout lands in the failure word
+  }
   BTA_CUDA_TRY(cudaMemsetAsync(fail_block, 0xff, sizeof(int32_t), stream));
-  bta_status st = factor_sweep(*q, rhs_inout, slots, fail_block, ws, stream);
+  bta_status st = factor_sweep(*q, rhs_inout, slots, fail_block, ws, stream, precision);
   if (st == BTA_OK) st = sum_slots(slots, nsl, logdet, 0, stream);
   cudaFreeAsync(buf, stream);
   if (st == BTA_OK) q->state = BTA_STATE_FACTORED;
@@ -537,19 +560,48 @@ bta_status bta_factor(bta_desc* q, double* rhs_inout, double* logdet, int32_t* f
 
 bta_status bta_solve(const bta_desc* L, double* z_inout, int32_t lower, int32_t refine,
                      const bta_desc* Q_or_null, cudaStream_t stream) {
-  (void)Q_or_null;
-  if (!desc_ok(L, 0) || !z_inout || refine != 0) return BTA_ERR_ARG;
+  if (!desc_ok(L, 0) || !z_inout || refine < 0 || refine > 1) return BTA_ERR_ARG;
+  if (refine) {   // needs r (lower = 1) and the assembled matrix of the same shape
+    const bta_desc* Q = Q_or_null;
+    if (!lower || !desc_ok(Q, 0) || Q->n != L->n || Q->b != L->b || Q->ld != L->ld ||
+        Q->a != L->a || Q->D == L->D)
+      return BTA_ERR_ARG;
+    if (Q->state != BTA_STATE_ASSEMBLED) return BTA_ERR_STATE;
+  }
   if (L->state != BTA_STATE_FACTORED) return BTA_ERR_STATE;
-  size_t wsb = SweepWs::bytes(L->ld, L->a);
+  const size_t wsb = SweepWs::bytes(L->ld, L->a);
+  const size_t nv = (size_t)L->n * L->ld + L->a;
   double* buf = nullptr;
-  BTA_CUDA_TRY(cudaMallocAsync(&buf, wsb, stream));
+  BTA_CUDA_TRY(cudaMallocAsync(&buf, wsb + (refine ? 2 * nv * sizeof(double) : 0), stream));
   SweepWs ws;
   ws.carve(buf, L->ld, L->a);
+  double* r = buf + wsb / sizeof(double);   // refinement: r, then the correction
+  double* dx = r + nv;
   bta_status st = BTA_OK;
-  if (lower) st = lower_solve(*L, z_inout, ws, stream);
+  if (refine)
+    st = copy_block(z_inout, (int)nv, r, (int)nv, (int)nv, 1, 1.0, 0, stream);
+  if (st == BTA_OK && lower) st = lower_solve(*L, z_inout, ws, stream);
   if (st == BTA_OK) st = upper_solve(*L, z_inout, ws, stream);
+  if (st == BTA_OK && refine) {
+    // one step of iterative refinement in FP64 (Eqs. 3-5 on the residual):
+    // x += Q^{-1} (r - Q x) with the factor L of Q
+    st = copy_block(r, (int)nv, dx, (int)nv, (int)nv, 1, 1.0, 0, stream);
+    if (st == BTA_OK) st = bta_residual(*Q_or_null, z_inout, dx, ws.gv, stream);
+    if (st == BTA_OK) st = lower_solve(*L, dx, ws, stream);
+    if (st == BTA_OK) st = upper_solve(*L, dx, ws, stream);
+    if (st == BTA_OK) st = launch_axpy((int64_t)nv, 1.0, dx, z_inout, stream);
+  }
   cudaFreeAsync(buf, stream);
   return st;
+}
+
+bta_status bta_set_wait_limit(int64_t limit_ns, int32_t stall) {
+  if (limit_ns < 0 || (limit_ns > 0 && limit_ns < 1000000) || limit_ns > 60000000000ll ||
+      (stall != 0 && stall != 1))
+    return BTA_ERR_ARG;
+  g_dag_wait_ns = limit_ns ? (unsigned long long)limit_ns : 2000000000ull;
+  g_dag_stall = stall;
+  return BTA_OK;
 }
 
 bta_status bta_selinv(bta_desc* L, inla_model* m, const double* theta, int32_t which,
@@ -641,8 +693,8 @@ bta_status inla_value_and_grad(inla_model* m, const double* theta, int32_t batch
     const int cnt = std::min(group, batch - i0);
     std::memcpy(m->htheta, theta + (size_t)i0 * d, (size_t)cnt * d * sizeof(double));
     bta_status s1 = run_group(m, mode, cnt, prec, use_graph, stream);
-    if (s1 != BTA_OK && s1 != BTA_ERR_NOT_SPD) return s1;
-    if (s1 != BTA_OK) st = s1;
+    if (s1 != BTA_OK && s1 != BTA_ERR_NOT_SPD && s1 != BTA_ERR_TIMEOUT) return s1;
+    st = worse(st, s1);
     for (int e = 0; e < cnt; ++e) {
       const double* o = m->hout + (size_t)e * no;
       f[i0 + e] = o[0];
@@ -800,14 +852,15 @@ bta_status inla_batch_value_and_grad(inla_batch* b, const double* theta, int32_t
   for (int i = 0; i < nm; ++i) {
     inla_model* m = b->models[i];
     const int no = out_size(m->d);
+    int32_t tcs = 0;
+    BTA_CUDA_TRY(cudaMemcpy(&tcs, m->ctx[0].fail + 2, sizeof(int32_t), cudaMemcpyDeviceToHost));
     m->last.assign(m->hout, m->hout + no);
     m->ctx[0].have_factors = g ? 0 : 1 + prec;
     m->launched += b->kernels[g][prec] / nm;
     f[i] = m->hout[0];
     if (grad)
       for (int j = 0; j < m->d; ++j) grad[(size_t)i * ldt + j] = m->hout[1 + j];
-    const double* parts = m->hout + 1 + m->d;
-    if (parts[6] >= 0 || parts[7] >= 0) st = BTA_ERR_NOT_SPD;
+    st = worse(st, eval_status(m->hout + 1 + m->d, tcs));
   }
   return st;
 }

@@ -75,6 +75,16 @@ cudaError_t launch_prio(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStr
 }
 
 inline int pad_ld(int b) { return (b + kPad - 1) / kPad * kPad; }
+
+// Streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount,
+// queried once per device): grids and tile plans are sized in waves of it.
+int sm_count();
+
+// Bound of every globaltimer wait in the task-graph factor (ns; 2 s unless a
+// test lowered it with bta_set_wait_limit), and the test switch that makes its
+// chain wait on a counter nothing sets.
+extern unsigned long long g_dag_wait_ns;
+extern int g_dag_stall;
 inline int cdiv(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
 
 // ----------------------------------------------------------------------------

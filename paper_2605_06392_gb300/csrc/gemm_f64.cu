@@ -263,11 +263,12 @@ __global__ void gemv_finish(GemvDev g) {
 // evaluation before a graph is captured) and never inside stream capture.
 // The tile does not change a product's bits: every tile sums K in the same
 // order and the ranges it skips hold exact zeros.
-using TuneKey = std::tuple<int, int, int, int, int, int, int, int, int, int, int>;
+// The measured choices form a process-wide cache (a table of hardware
+// timings, keyed by device, guarded by a mutex); the scratch operands of a
+// timing are allocated on the stream for that timing alone.
+using TuneKey = std::tuple<int, int, int, int, int, int, int, int, int, int, int, int>;
 std::mutex g_tune_mu;
 std::map<TuneKey, int> g_tuned;
-double* g_tscratch = nullptr;
-size_t g_tscratch_n = 0;
 thread_local int g_tune_depth = 0;
 
 bool autotune_on() {
@@ -289,10 +290,10 @@ bta_status gemm_f64(const Gemm& g, cudaStream_t s) {
   const int nb = g.batch;
   const int K = g.K > 0 ? g.K : 0;
   // Tile choice.  Every tile is FP64-pipe bound and the hardware spreads
-  // tiles evenly over the 152 SMs, so an op takes about
-  // ceil(tiles / 152) x (BM x BN x K) / rate: pick the shape minimising that
+  // tiles evenly over the SMs, so an op takes about
+  // ceil(tiles / SMs) x (BM x BN x K) / rate: pick the shape minimising that
   // (16 x 16 tiles pay ~5 % more for their shared-memory traffic per FMA).
-  constexpr int kSMs = 152;
+  const int kSMs = sm_count();
   auto units = [&](int bm, int bn, int count) -> int64_t {
     const int tm = cdiv(g.M, bm), tn = cdiv(g.N, bn);
     int64_t u = 0;
@@ -390,7 +391,9 @@ bta_status gemm_f64(const Gemm& g, cudaStream_t s) {
     return BTA_OK;
   };
   if (bm != 0 && autotune_on()) {
-    const TuneKey key{g.M, g.N, K, g.lda, g.ldb, g.transA, g.transB, g.triA, g.triB,
+    int dev = 0;
+    BTA_CUDA_TRY(cudaGetDevice(&dev));
+    const TuneKey key{dev, g.M, g.N, K, g.lda, g.ldb, g.transA, g.transB, g.triA, g.triB,
                       g.out_lower, np};
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tuned.find(key);
@@ -403,19 +406,14 @@ bta_status gemm_f64(const Gemm& g, cudaStream_t s) {
       const size_t fb = (size_t)g.ldb * (g.transB ? std::max(K, 1) : g.N);
       const size_t fc = std::max((size_t)g.ldc * g.N, (size_t)g.M * g.N);
       const size_t need = fa + fb + fc;
-      if (need > g_tscratch_n) {
-        if (g_tscratch) cudaFree(g_tscratch);
-        g_tscratch = nullptr;
-        g_tscratch_n = 0;
-        BTA_CUDA_TRY(cudaMalloc(&g_tscratch, need * sizeof(double)));
-        BTA_CUDA_TRY(cudaMemset(g_tscratch, 0, need * sizeof(double)));
-        g_tscratch_n = need;
-      }
+      double* scratch = nullptr;
+      BTA_CUDA_TRY(cudaMallocAsync(&scratch, need * sizeof(double), s));
+      BTA_CUDA_TRY(cudaMemsetAsync(scratch, 0, need * sizeof(double), s));
       std::vector<Prob> P(probs);
       for (Prob& q : P) {
-        q.A = g_tscratch;
-        q.B = g_tscratch + fa;
-        q.C = g_tscratch + fa + fb;
+        q.A = scratch;
+        q.B = scratch + fa;
+        q.C = scratch + fa + fb;
         q.Cin = q.Cin ? q.C : nullptr;
       }
       cudaEvent_t e0, e1;
@@ -438,6 +436,7 @@ bta_status gemm_f64(const Gemm& g, cudaStream_t s) {
       }
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
+      BTA_CUDA_TRY(cudaFreeAsync(scratch, s));
       it = g_tuned.emplace(key, best).first;
     }
     if (it != g_tuned.end()) bm = it->second;

@@ -1,6 +1,6 @@
 // bta_factor_noalloc: the block factorisation of bta_factor, run out of a
-// fixed scratch area that the library reserves in device memory when it is
-// loaded, so the call itself never allocates.
+// fixed scratch area in the library's device memory (a static __device__
+// array), so the call itself never allocates.
 //
 // Who needs this: callers that cannot allocate device memory while they run
 // the factorisation.  Examples are a serving process that has handed the
@@ -14,8 +14,8 @@
 //
 // Limits (checked, BTA_ERR_ARG beyond them): ld <= 256, a <= 32, and
 // n * (ld / 32) + 1 <= 16384 log-determinant slots (n <= 2047 at ld = 256).
-// The array holds 2.4 MB and stays resident on every GPU that loads the
-// library until the process exits.
+// The array holds 2.4 MB and, once reserved on a GPU, stays there until the
+// process exits.
 //
 // Sharing: all calls on a device use the same array.  Calls that overlap on
 // the GPU (different streams, or different host threads without ordering)
@@ -24,11 +24,13 @@
 // (every work block and slot is written before it is read, and the sweep
 // clears its arrow accumulator itself).
 //
-// Set-up: the first call on each device looks up the device address of the
-// array (cudaGetSymbolAddress, with that device current) and caches it; make
-// that first call before any stream capture on the device.
-#include <mutex>
-
+// Set-up: every call looks up the device address of the array on the
+// current device (cudaGetSymbolAddress), so a device reset cannot leave a
+// stale address behind.  Under CUDA's lazy module loading the first lookup on
+// a device loads this file's device code and reserves the array there: that
+// first call can itself allocate device memory and synchronise.  Callers on a
+// strict budget should therefore make one call at set-up time, before any
+// stream capture; later calls find the array in place and allocate nothing.
 #include "sweep.cuh"
 
 namespace {
@@ -47,27 +49,19 @@ constexpr size_t kScratchDoubles = kWorkDoubles + kNoAllocMaxSlots;
 
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-double* g_addr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device (cached per device).
+// Device address of the scratch array on the current device.  In host code
+// g_noalloc_scratch names a host-side stand-in, never the device memory; only
+// this lookup gives the address a kernel may use.
 bta_status scratch_address(double** out) {
-  int dev = -1;
-  BTA_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) return BTA_ERR_ARG;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      fprintf(stderr, "[bta] bta_factor_noalloc: cudaGetSymbolAddress failed: %s\n",
-              cudaGetErrorString(e));
-      return BTA_ERR_CUDA;
-    }
-    g_addr[dev] = static_cast<double*>(p);
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p) {
+    cudaGetLastError();
+    fprintf(stderr, "[bta] bta_factor_noalloc: cudaGetSymbolAddress failed: %s\n",
+            cudaGetErrorString(e));
+    return BTA_ERR_CUDA;
   }
-  *out = g_addr[dev];
+  *out = static_cast<double*>(p);
   return BTA_OK;
 }
 

@@ -47,6 +47,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdlib>
 
 #include "common.cuh"
@@ -958,7 +959,6 @@ struct OzPlan {
   bool n128 = false;
   int splits = 1;
 };
-constexpr int kSmCount = 152;
 constexpr int kMaxSplits = 16;
 constexpr int kCtaFixedSlabs = 4;
 
@@ -969,6 +969,7 @@ OzPlan oz_plan(int M, int N, int K, int S) {
   }();
   OzPlan p;
   if (S != 8 || force == 0) return p;
+  const int kSmCount = sm_count();
   const int64_t nk = cdiv(K, OK16);
   const int64_t t64 = (int64_t)cdiv(M, OM) * cdiv(N, OBN);
   const int64_t t128 = (int64_t)cdiv(M, OM) * cdiv(N, QN);
@@ -1055,7 +1056,8 @@ bta_status launch_ozaki(const Gemm& g, uint8_t* ws, int32_t* status, cudaStream_
     q.out_lower = g.out_lower;
     q.partial = partial;
     q.status = status;
-    q.group = std::min(L.Mp / OM, 12);   // ~sqrt(152): a wave spans ~12 x 13 tiles
+    // ~sqrt(SMs) tile rows a group: a wave of CTAs spans a near-square patch
+    q.group = std::min(L.Mp / OM, std::max(1, (int)std::lround(std::sqrt((double)sm_count()))));
     ozaki_gemm128_kernel<<<dim3((L.Mp / OM) * (L.Np / QN), 1, plan.splits), kQThreads, kQSmem,
                            s>>>(mA, mB, q);
     BTA_LAUNCHED();
@@ -1098,7 +1100,7 @@ size_t ozaki_ws_bytes(int M, int N, int K, int slices) {
   const size_t Mq = (size_t)cdiv(M, OM) * OM, Nq = (size_t)cdiv(N, QN) * QN;
   const size_t Kp = (size_t)cdiv(K, OK16) * OK16;
   auto up = [](size_t x) { return (x + 255) / 256 * 256; };
-  const size_t part = std::max(Mq * Nq, (size_t)kSmCount * OM * QN) * 8;
+  const size_t part = std::max(Mq * Nq, (size_t)sm_count() * OM * QN) * 8;
   const size_t t128 = up(8 * Mq * Kp * 2) + up(8 * Nq * Kp * 2) + up(Mq * 4) + up(Nq * 4) +
                       up(part) + 256;
   return std::max(t64, t128);

@@ -23,10 +23,12 @@
 // so the graph always drains.  Per-tile counters (W updates applied, R
 // updates applied, F/S/G done) are published with release stores after the
 // tile is written and read with acquire loads; tile data are read through
-// L2 (ld.global.cg).  Every wait is bounded by a 2 s globaltimer limit; on
-// expiry the CTA raises a shared abort flag, records the timeout code in the
-// block's failure word and returns, and every other CTA returns at its next
-// wait.
+// L2 (ld.global.cg).  Every wait is bounded by a globaltimer limit (2 s); on
+// expiry the CTA raises a shared abort flag, writes BTA_ERR_TIMEOUT into the
+// block's failure word (which otherwise holds -1 or the index of a block with
+// a non-positive pivot) and returns, and every other CTA returns at its next
+// wait.  A test switch (bta_set_wait_limit) lowers the limit and makes the
+// chain wait on a counter nothing sets, so that this path runs without a fault.
 #include <algorithm>
 #include <cstdlib>
 #include <vector>
@@ -39,8 +41,6 @@ namespace {
 constexpr int T = kPad;                 // tile size
 constexpr int kDagThreads = 256;
 constexpr int kMaxP = 160;              // tile rows supported (ld <= 5120)
-constexpr unsigned long long kWaitNs = 2000000000ull;
-constexpr int32_t kFailTimeout = 0x40000000;
 
 enum : int { TK_H = 0, TK_S = 1, TK_G = 2, TK_U = 3, TK_V = 4 };
 
@@ -60,6 +60,8 @@ struct DagArgs {
   int* abort;               // shared abort flag
   int* smbusy;              // per SM: chain tasks running there (see TK_H)
   int yield;                // bulk tasks wait while a chain task holds their SM
+  int stall;                // test switch: the chain waits on a counter nothing sets
+  unsigned long long wait_ns;   // bound of every wait
   int off[kMaxP + 1];       // task offset of each step within one instance
   DagInst inst[kMaxBatch];
 };
@@ -83,15 +85,15 @@ __device__ __forceinline__ unsigned long long now_ns() {
   return t;
 }
 
-// Thread 0 waits until *p >= need (bounded); false on timeout / abort.
-__device__ bool wait_ge(const int* p, int need, int* abort) {
+// Thread 0 waits until *p >= need (bounded by wait_ns); false on timeout / abort.
+__device__ bool wait_ge(const int* p, int need, int* abort, unsigned long long wait_ns) {
   if (ld_acquire(p) >= need) return true;
   const unsigned long long t0 = now_ns();
   while (true) {
     __nanosleep(64);
     if (ld_acquire(p) >= need) return true;
     if (ld_acquire(abort)) return false;
-    if (now_ns() - t0 > kWaitNs) {
+    if (now_ns() - t0 > wait_ns) {
       atomicExch(abort, 1);
       return false;
     }
@@ -402,7 +404,7 @@ __global__ void __launch_bounds__(kDagThreads) potrf_dag_kernel(DagArgs g) {
         const unsigned long long t0 = now_ns();
         while (ld_acquire(busy) > 0 && ld_acquire(g.counter) < g.total && !ld_acquire(g.abort)) {
           __nanosleep(256);
-          if (now_ns() - t0 > kWaitNs) {
+          if (now_ns() - t0 > g.wait_ns) {
             atomicExch(g.abort, 1);
             break;
           }
@@ -427,19 +429,23 @@ __global__ void __launch_bounds__(kDagThreads) potrf_dag_kernel(DagArgs g) {
       // ---- the chain: every diagonal step of this block on this CTA
       if (threadIdx.x == 0 && g.yield) atomicAdd(busy, 1);
       for (int c = 0; c < p; ++c) {
-        if (c > 0) {
-          // W_{c,c-1} and W_cc updated through step c-2 by the U tasks
+        if (c > 0 || g.stall) {
+          // W_{c,c-1} and W_cc updated through step c-2 by the U tasks (the
+          // test switch instead waits for a count no task reaches)
           if (threadIdx.x == 0)
-            s_ok = wait_ge(&cntW[c * p + c - 1], c - 1, g.abort) &&
-                   wait_ge(&cntW[c * p + c], c - 1, g.abort);
+            s_ok = g.stall ? wait_ge(&cntW[c * p + c], 0x7fffffff, g.abort, g.wait_ns)
+                           : wait_ge(&cntW[c * p + c - 1], c - 1, g.abort, g.wait_ns) &&
+                             wait_ge(&cntW[c * p + c], c - 1, g.abort, g.wait_ns);
           __syncthreads();
           if (!s_ok) {
             if (threadIdx.x == 0) {
-              atomicCAS(I.fail, -1, kFailTimeout);
+              atomicExch(I.fail, (int32_t)BTA_ERR_TIMEOUT);
               if (g.yield) atomicSub(busy, 1);
             }
             return;
           }
+        }
+        if (c > 0) {
           load_tile(S0, tile(I.A, ld, c, c - 1), ld);
           // W_cc into registers now, into S0 once the product has read it
           double wcc[T * T / kDagThreads];
@@ -487,25 +493,26 @@ __global__ void __launch_bounds__(kDagThreads) potrf_dag_kernel(DagArgs g) {
       bool ok = true;
       switch (t.type) {
         case TK_S:
-          ok = wait_ge(&doneF[t.k], 1, g.abort) && wait_ge(&cntW[t.i * p + t.k], t.k, g.abort);
+          ok = wait_ge(&doneF[t.k], 1, g.abort, g.wait_ns) &&
+               wait_ge(&cntW[t.i * p + t.k], t.k, g.abort, g.wait_ns);
           break;
         case TK_G:
-          ok = wait_ge(&doneF[t.i], 1, g.abort) &&
-               wait_ge(&cntR[t.i * p + t.j], t.i - t.j, g.abort);
+          ok = wait_ge(&doneF[t.i], 1, g.abort, g.wait_ns) &&
+               wait_ge(&cntR[t.i * p + t.j], t.i - t.j, g.abort, g.wait_ns);
           break;
         case TK_U:
-          ok = wait_ge(&doneS[t.i * p + t.k], 1, g.abort) &&
-               wait_ge(&doneS[t.j * p + t.k], 1, g.abort) &&
-               wait_ge(&cntW[t.i * p + t.j], t.k, g.abort);
+          ok = wait_ge(&doneS[t.i * p + t.k], 1, g.abort, g.wait_ns) &&
+               wait_ge(&doneS[t.j * p + t.k], 1, g.abort, g.wait_ns) &&
+               wait_ge(&cntW[t.i * p + t.j], t.k, g.abort, g.wait_ns);
           break;
         default:   // TK_V
-          ok = wait_ge(&doneS[t.i * p + t.k], 1, g.abort) &&
-               (t.j == t.k ? wait_ge(&doneF[t.k], 1, g.abort)
-                           : wait_ge(&doneG[t.k * p + t.j], 1, g.abort)) &&
-               wait_ge(&cntR[t.i * p + t.j], t.k - t.j, g.abort);
+          ok = wait_ge(&doneS[t.i * p + t.k], 1, g.abort, g.wait_ns) &&
+               (t.j == t.k ? wait_ge(&doneF[t.k], 1, g.abort, g.wait_ns)
+                           : wait_ge(&doneG[t.k * p + t.j], 1, g.abort, g.wait_ns)) &&
+               wait_ge(&cntR[t.i * p + t.j], t.k - t.j, g.abort, g.wait_ns);
       }
       s_ok = ok;
-      if (!ok) atomicCAS(I.fail, -1, kFailTimeout);
+      if (!ok) atomicExch(I.fail, (int32_t)BTA_ERR_TIMEOUT);
     }
     __syncthreads();
     if (!s_ok) return;
@@ -595,7 +602,19 @@ int dag_yield() {
   return v;
 }
 
+__global__ void pivot_reciprocals_kernel(const double* __restrict__ v, int64_t n,
+                                         double* __restrict__ r, double* __restrict__ q) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    if (r) r[i] = recip(v[i]);
+    if (q) q[i] = rsqrt_fp64(v[i]);
+  }
+}
+
 }  // namespace
+
+unsigned long long g_dag_wait_ns = 2000000000ull;
+int g_dag_stall = 0;
 
 int potrf_dag_tasks(int p) {
   int tot = 1;
@@ -639,7 +658,9 @@ bta_status potrf_dag_batch(int count, double* const* A, int n, int ld, double* c
     g.abort = g.counter + 16;
     g.smbusy = g.inst[0].st + 4 * p * p + p + 64;
     g.yield = cnt <= 2 ? dag_yield() : 0;
-    const int grid = std::min(g.total, 152 * dag_ctas_per_sm());
+    g.stall = g_dag_stall;
+    g.wait_ns = g_dag_wait_ns;
+    const int grid = std::min(g.total, sm_count() * dag_ctas_per_sm());
     launch_prio(potrf_dag_kernel, dim3(grid), dim3(kDagThreads), s, g);
     BTA_LAUNCHED();
   }
@@ -647,3 +668,14 @@ bta_status potrf_dag_batch(int count, double* const* A, int n, int ld, double* c
 }
 
 }  // namespace bta
+
+extern "C" bta_status bta_pivot_reciprocals(const double* v, int64_t n, double* recip_out,
+                                            double* rsqrt_out, cudaStream_t stream) {
+  if (n < 0 || (n > 0 && !v) || (!recip_out && !rsqrt_out)) return BTA_ERR_ARG;
+  if (n == 0) return BTA_OK;
+  const int64_t blocks = (n + 255) / 256;
+  if (blocks > 0x7fffffff) return BTA_ERR_ARG;
+  bta::pivot_reciprocals_kernel<<<(unsigned)blocks, 256, 0, stream>>>(v, n, recip_out, rsqrt_out);
+  BTA_LAUNCHED();
+  return BTA_OK;
+}

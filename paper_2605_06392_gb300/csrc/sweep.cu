@@ -133,11 +133,29 @@ __global__ void sum_kernel(const double* parts, int n, double* out, int acc) {
 
 }  // namespace
 
+int sm_count() {
+  static int cache[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    dev = 0;
+  }
+  int* slot = dev >= 0 && dev < 64 ? &cache[dev] : nullptr;
+  if (slot && *slot > 0) return *slot;
+  int v = 0;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) {
+    cudaGetLastError();
+    v = 1;
+  }
+  if (slot) *slot = v;
+  return v;
+}
+
 bta_status copy_block(const double* src, int lds, double* dst, int ldd, int rows, int cols,
                       double alpha, int mode, cudaStream_t s) {
   int64_t n = (int64_t)rows * cols;
   if (n <= 0) return BTA_OK;
-  int grid = (int)std::min<int64_t>(cdiv(n, 256), 4 * 152 * 8);
+  int grid = (int)std::min<int64_t>(cdiv(n, 256), 32 * sm_count());
   copy_kernel<<<grid, 256, 0, s>>>(src, lds, dst, ldd, rows, cols, alpha, mode);
   BTA_LAUNCHED();
   return BTA_OK;
@@ -155,7 +173,7 @@ bta_status copy_block_batch(int count, const double* const* src, int lds, double
       d.src[z] = src[z0 + z];
       d.dst[z] = dst[z0 + z];
     }
-    int gx = (int)std::min<int64_t>(cdiv(n, 256), std::max(1, 4 * 152 * 8 / cnt));
+    int gx = (int)std::min<int64_t>(cdiv(n, 256), std::max(1, 32 * sm_count() / cnt));
     copy_batch_kernel<<<dim3(gx, cnt), 256, 0, s>>>(d);
     BTA_LAUNCHED();
   }
@@ -164,7 +182,7 @@ bta_status copy_block_batch(int count, const double* const* src, int lds, double
 
 bta_status fill_value(double* p, int64_t n, double v, cudaStream_t s) {
   if (n <= 0) return BTA_OK;
-  int grid = (int)std::min<int64_t>(cdiv(n, 256), 4 * 152 * 8);
+  int grid = (int)std::min<int64_t>(cdiv(n, 256), 32 * sm_count());
   fill_kernel<<<grid, 256, 0, s>>>(p, n, v);
   BTA_LAUNCHED();
   return BTA_OK;
@@ -412,10 +430,63 @@ bta_status factor_sweep_multi(const SweepItem* it, int m, cudaStream_t s, cudaEv
 }
 
 bta_status factor_sweep(const bta_desc& q, double* rhs, double* slots, int32_t* fail,
-                        const SweepWs& ws, cudaStream_t s) {
+                        const SweepWs& ws, cudaStream_t s, int precision) {
   SweepItem item;
   item.q = q; item.vec = rhs; item.slots = slots; item.fail = fail; item.ws = ws;
-  return factor_sweep_multi(&item, 1, s);
+  return factor_sweep_multi(&item, 1, s, nullptr, precision);
+}
+
+// ----------------------------------------------------------------------------
+// Residual d - Q x of an assembled BTA matrix (the refinement step of
+// bta_solve), as GEMVs on its blocks.  D_i is stored as its lower triangle:
+// D_i x = L x + L^T x - diag(D_i) x with L the stored lower part.
+// ----------------------------------------------------------------------------
+namespace {
+__global__ void diag_axpy_kernel(const double* __restrict__ D, int ld, const double* x,
+                                 double* y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < ld) y[i] = fma(D[i + (int64_t)i * ld], x[i], y[i]);
+}
+}  // namespace
+
+bta_status bta_residual(const bta_desc& q, const double* x, double* d, double* gv,
+                        cudaStream_t s) {
+  const int n = q.n, ld = q.ld, a = q.a;
+  const int64_t blk = (int64_t)ld * ld;
+  const double* xT = x + (int64_t)n * ld;
+  double* dT = d + (int64_t)n * ld;
+  for (int i = 0; i < n; ++i) {
+    const double* xi = x + (int64_t)i * ld;
+    double* di = d + (int64_t)i * ld;
+    const double* Di = q.D + i * blk;
+    auto minus = [&](const double* A, int lda, int M, int K, int trans, int tri,
+                     const double* v, double* y) {
+      Gemv g; g.M = M; g.K = K; g.A = A; g.lda = lda; g.transA = trans; g.triA = tri;
+      g.x = v; g.y = y; g.yin = y; g.alpha = -1.0; g.beta = 1.0;
+      return gemv_f64(g, gv, s);
+    };
+    BTA_TRY(minus(Di, ld, ld, ld, 0, TRI_LOWER, xi, di));          // - L x
+    BTA_TRY(minus(Di, ld, ld, ld, 1, TRI_UPPER, xi, di));          // - L^T x
+    diag_axpy_kernel<<<cdiv(ld, 256), 256, 0, s>>>(Di, ld, xi, di);   // + diag x
+    BTA_LAUNCHED();
+    if (i > 0) BTA_TRY(minus(q.B + (i - 1) * blk, ld, ld, ld, 0, TRI_NONE, xi - ld, di));
+    if (i < n - 1) BTA_TRY(minus(q.B + i * blk, ld, ld, ld, 1, TRI_NONE, xi + ld, di));
+    if (a > 0) {
+      const double* Ci = q.C + (int64_t)i * a * ld;
+      BTA_TRY(minus(Ci, a, ld, a, 1, TRI_NONE, xT, di));           // - C_i^T x_T
+      BTA_TRY(minus(Ci, a, a, ld, 0, TRI_NONE, xi, dT));           // tip row: - C_i x_i
+    }
+  }
+  if (a > 0) {   // - T x_T (lower triangle referenced, as D)
+    Gemv g; g.M = a; g.K = a; g.A = q.T; g.lda = a; g.triA = TRI_LOWER;
+    g.x = xT; g.y = dT; g.yin = dT; g.alpha = -1.0; g.beta = 1.0;
+    BTA_TRY(gemv_f64(g, gv, s));
+    g.transA = 1; g.triA = TRI_UPPER;
+    BTA_TRY(gemv_f64(g, gv, s));
+    diag_axpy_kernel<<<1, 32, 0, s>>>(q.T, a, xT, dT);
+    BTA_LAUNCHED();
+  }
+  return BTA_OK;
 }
 
 // ----------------------------------------------------------------------------

@@ -59,7 +59,11 @@ bta_status upper_solve_multi(const SweepItem* items, int m, cudaStream_t s);
 bta_status selinv_sweep_multi(const SweepItem* items, int m, cudaStream_t s, int precision = 0);
 
 bta_status factor_sweep(const bta_desc& q, double* rhs, double* slots, int32_t* fail,
-                        const SweepWs& ws, cudaStream_t s);
+                        const SweepWs& ws, cudaStream_t s, int precision = 0);
+// d <- d - Q x for an assembled BTA matrix Q (D lower triangle referenced, B,
+// C, T as in bta_desc); x, d: n*ld + a.  gv: GEMV work of kGemvSplit * ld.
+bta_status bta_residual(const bta_desc& q, const double* x, double* d, double* gv,
+                        cudaStream_t s);
 bta_status lower_solve(const bta_desc& q, double* z, const SweepWs& ws, cudaStream_t s);
 bta_status upper_solve(const bta_desc& q, double* z, const SweepWs& ws, cudaStream_t s);
 bta_status tip_forward(const bta_desc& q, double* rT, const double* vT, cudaStream_t s);
