@@ -1,17 +1,23 @@
 """Benchmark: INLA f + grad evaluations per second on one GB300.
 
-Workload: univariate spatio-temporal model on a 32x32 grid (b = 1024),
-n_t = 50 time blocks, a = 6 fixed effects, d = 4, 1e5 observations
-(seeded synthetic data).  One step = one call of inla_value_and_grad (all
-of the hot path: assembly of Q_p and Q_c, both BTA factorisations, the
+Headline workload: the production-scale coregionalised model -- 3 responses
+on a 40x40 grid each (b = 4800), n_t = 192 time blocks, a = 12 fixed effects,
+d = 15 hyperparameters, 2e6 observations (seeded synthetic data shaped like
+the paper's SA1 model, Table I).  One step = one call of inla_value_and_grad
+(all of the hot path: assembly of Q_p and Q_c, both BTA factorisations, the
 solve for x*, f, both in-place selected inversions with the fused Phase A/C
-traces, Phase B and the explicit terms).  The working set (two factors of
-0.84 GB each) is far larger than L2, so no flush is needed between steps.
+traces, Phase B and the explicit terms) in emulated FP64: every b x b product
+computed to FP64 accuracy from 8 BF16 slices on the tensor cores, everything
+else in FP64.  The working set (two factors of 70.7 GB) is far larger than
+L2, so no flush is needed between steps.
 
-Also reported: the 2d+1 central finite-difference gradient (value-only
-evaluations) on the same GPU, the FP64 efficiency of the whole step, the
-roofline of the dominant kernel (the FP64 tile GEMM at the sweep's block
-shape, timed live), and the FP64 CPU oracle on a bounded sample.
+Also reported: the 2d+1 = 31-point central finite-difference gradient
+(value-only evaluations) of the same model on the same GPU, the roofline of
+the dominant kernel (the emulated product's tensor-core kernel at the
+sweep's block shape, timed live), log|Q_p| against its spectral closed form,
+the 32x32-grid univariate model (b = 1024, n_t = 50, d = 4) in all three
+precisions with its own FD comparison, and the FP64 CPU oracle on a bounded
+cut of the headline model.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -20,6 +26,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import statistics
 import subprocess
 import sys
 import threading
@@ -32,10 +39,10 @@ import numpy as np  # noqa: E402
 
 METRIC = "INLA f+∇f evals/s on 1 GB300: AD vs 2d+1 FD; % FP64 TC peak; rel err vs FP64"
 UNIT = "gradient evaluations/s"
-WORKLOAD = "st_medium"
-# FP64 peak of the arithmetic unit the path uses (DFMA, "alu"): 152 SMs x 2 FP64
-# FMA/clock/SM x 2 flop x 2.07 GHz maximum SM clock.
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+WORKLOAD = "coreg_production"      # 3 x 40x40 grid, b = 4800, n_t = 192, a = 12, d = 15
+SIDE = "st_medium"                 # 32x32 grid, b = 1024, n_t = 50, a = 6, d = 4
+PRECISION = 2                      # emulated FP64 (BF16 slices on tcgen05)
+PAIRS = 36                         # BF16 slice products per emulated FP64 product
 
 
 def reduce_replicas(times, dist=None, device="cpu"):
@@ -50,6 +57,26 @@ def reduce_replicas(times, dist=None, device="cpu"):
     return [float(v) for v in tt.tolist()]
 
 
+def measured_peaks():
+    """The machine's measured copy bandwidth and BF16 rates (MEASURED_PEAKS.json,
+    written by the driver), else the stated fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return {"hbm_gbs": float(p["hbm_gbs"]), "bf16_tflops": float(p["bf16_tflops"]),
+                "bf16_tflops_sustained": float(p["bf16_tflops_sustained"]),
+                "sm_max_mhz": float(p.get("sm_max_mhz", 2070.0)), "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+def fp64_peak_tflops(sm_count, sm_mhz):
+    """FP64 peak of the DFMA pipe the FP64 path runs on: SMs x 2 FP64 FMA per
+    clock per SM x 2 flop x the maximum SM clock."""
+    return sm_count * 2 * 2 * sm_mhz * 1e6 / 1e12
+
+
 def _flops_model(b, n, a):
     """Algorithmic FP64 flops of one f+grad and of one value-only evaluation
     with the block kernels as implemented (per matrix and block: factor
@@ -61,12 +88,37 @@ def _flops_model(b, n, a):
     return fwd + bwd, fwd
 
 
+def spectral_logdet_prior(prob):
+    """log|Q_p| of a model with C = I in closed form: every factor is a
+    polynomial in the grid Laplacian (eigenvalues 2 - 2 cos(pi p / m) per
+    axis) and in M1 = tridiag(-1, 2, -1) (2 - 2 cos(pi j / (n + 1))), so each
+    eigenvalue of a variable's Q_st is s [(kappa^2 + mu)^2 + 2 kappa gamma nu
+    (kappa^2 + mu) + 1]; the coregionalisation adds -2 n ns sum log sigma_m
+    and the fixed-effect tip a log 1e-3."""
+    def path(m):
+        return 2.0 - 2.0 * np.cos(np.pi * np.arange(m) / m)
+    mu = (path(prob.nx)[None, :] + path(prob.ny)[:, None]).reshape(1, -1)
+    nu = (2.0 - 2.0 * np.cos(np.pi * np.arange(1, prob.nt + 1) / (prob.nt + 1)))[:, None]
+    th, k = prob.theta, prob.k
+    if k == 1:
+        s, kap, gam = np.exp(th[0]), np.exp(th[1]), np.exp(th[2])
+        u = kap ** 2 + mu
+        return float(np.sum(np.log(s * (u * u + 2 * kap * gam * nu * u + 1.0)))) + \
+            prob.a * np.log(1e-3)
+    tot = 0.0
+    for m in range(k):
+        kap, gam = np.exp(th[m]), np.exp(th[k + m])
+        u = kap ** 2 + mu
+        tot += float(np.sum(np.log(u * u + 2 * kap * gam * nu * u + 1.0)))
+    tot -= 2.0 * prob.nt * prob.ns * float(np.sum(th[2 * k:3 * k]))
+    return tot + prob.a * np.log(1e-3)
+
+
 class ClockSampler:
     """nvidia-smi samples during the timed region."""
 
     def __init__(self):
         self.rows = []
-        self._stop = threading.Event()
         self._proc = None
 
     def start(self):
@@ -110,49 +162,96 @@ class ClockSampler:
                 "samples": len(self.rows)}
 
 
-def cpu_baseline(seconds_hint: float = 20.0):
-    """The FP64 oracle's block sweep (f and gradient) on a bounded sample of
-    the workload: the same 32x32-grid model with 6 of its 50 time blocks;
-    the per-block cost is constant, so the full-size time is the sample's
-    time x 50/6."""
+# ----------------------------------------------------------------------------
+# the FP64 CPU oracle (cpu_baseline and the reference arm)
+# ----------------------------------------------------------------------------
+FULL_NT = 192
+
+
+def oracle_cut_problem(nt):
+    """The headline model cut to nt of its 192 time blocks, with the
+    observations per time block kept (2e6 x nt / 192 rows)."""
     import workloads
+    full = workloads.WORKLOADS[WORKLOAD]
+    return workloads.make_problem(WORKLOAD, nt=nt,
+                                  n_obs=int(full["n_obs"]) * nt // int(full["nt"]))
+
+
+def oracle_step_seconds(prob):
+    """One f+grad of the oracle's block sweep on prob (wall seconds)."""
     from oracle import bta
-    prob = workloads.make_problem("st_medium_nt6")
     t0 = time.perf_counter()
     bta.evaluate(prob)
-    dt = time.perf_counter() - t0
-    full = workloads.WORKLOADS[WORKLOAD]["nt"]
-    t_full = dt * full / prob.nt
-    return {"value": 1.0 / t_full, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"oracle f+grad on the {WORKLOAD} model cut to nt={prob.nt} of {full} "
-                      f"time blocks ({dt:.1f} s), scaled by {full}/{prob.nt}",
-            "seconds_per_gradient": t_full}
+    return time.perf_counter() - t0
+
+
+def oracle_gradient_seconds(t1, t2):
+    """Seconds of one f+grad of the full 192-block model from the oracle's
+    times on cuts of 1 and 2 blocks: the first block has no sub-diagonal
+    block, and every further block adds the same work (one diagonal and one
+    sub-diagonal block of both matrices), t2 - t1."""
+    return t1 + (FULL_NT - 1) * (t2 - t1)
+
+
+def _oracle_sample_text(t1s, t2s):
+    t1, t2 = statistics.median(t1s), statistics.median(t2s)
+    return (f"oracle (FP64 block sweep, NumPy/SciPy) f+grad on the {WORKLOAD} model (b = 4800, "
+            f"d = 15) cut to 1 and to 2 of its {FULL_NT} time blocks, observations per block "
+            f"kept, {len(t1s)} run(s) each: medians {t1:.2f} s and {t2:.2f} s (ranges "
+            f"{min(t1s):.2f}-{max(t1s):.2f} s, {min(t2s):.2f}-{max(t2s):.2f} s); seconds per "
+            f"full gradient = t1 + {FULL_NT - 1} x (t2 - t1) = "
+            f"{oracle_gradient_seconds(t1, t2):.0f} s")
+
+
+def cpu_baseline(runs=1):
+    p1, p2 = oracle_cut_problem(1), oracle_cut_problem(2)
+    t1s = [oracle_step_seconds(p1) for _ in range(runs)]
+    t2s = [oracle_step_seconds(p2) for _ in range(runs)]
+    tg = oracle_gradient_seconds(statistics.median(t1s), statistics.median(t2s))
+    return {"value": 1.0 / tg, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": _oracle_sample_text(t1s, t2s), "seconds_per_gradient": tg}
 
 
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle on the machine's host cores (rank 0
+    only).  Each step evaluates f+grad on the 1-block and on the 2-block cut
+    of the headline model; the full model's time follows from the two."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    times = []
-    cb = None
+    p1, p2 = oracle_cut_problem(1), oracle_cut_problem(2)
+    t1s, t2s = [], []
     for i in range(args.warmup + args.steps):
-        cb = cpu_baseline()
+        a, b = oracle_step_seconds(p1), oracle_step_seconds(p2)
         if i >= args.warmup:
-            times.append(cb["seconds_per_gradient"])
-    t = float(np.mean(times))
-    line = {"impl": "reference", "metric": METRIC, "value": 1.0 / t, "unit": UNIT,
+            t1s.append(a)
+            t2s.append(b)
+    tg = oracle_gradient_seconds(statistics.median(t1s), statistics.median(t2s))
+    value = 1.0 / tg
+    steps = [a + b for a, b in zip(t1s, t2s)]
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": "32x32", "b": 1024, "nt": 50, "a": 6,
-                       "d": 4, "n_obs": 100000},
-            "cpu_baseline": {"value": 1.0 / t, "unit": UNIT, "cores": cb["cores"],
-                             "kind": "oracle", "sample": cb["sample"]},
-            "e2e": {"value": 1.0 / t, "unit": UNIT, "h2d_bytes_per_step": 0,
+            "ms_per_step": 1e3 * float(np.mean(steps)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{WORKLOAD} (each step: the oracle on cuts of 1 and 2 of "
+                                   f"its {FULL_NT} time blocks; value = 1 / (t1 + "
+                                   f"{FULL_NT - 1} (t2 - t1)) from the medians)",
+                       "grid": "3 x 40x40", "b": 4800, "nt": FULL_NT, "a": 12, "d": 15,
+                       "n_obs": 2_000_000, "cut_nt": [1, 2]},
+            "step_seconds": {"t1_median": statistics.median(t1s), "t1_min": min(t1s),
+                             "t1_max": max(t1s), "t2_median": statistics.median(t2s),
+                             "t2_min": min(t2s), "t2_max": max(t2s)},
+            "seconds_per_gradient": tg,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(),
+                             "kind": "oracle", "sample": _oracle_sample_text(t1s, t2s)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------------------
+# kernel-level measurements
+# ----------------------------------------------------------------------------
 def gemm_roofline(P, torch, b, reps=5, mixed=0):
     """Average duration of the FP64 tile GEMM (mixed=1: the split-TF32
     tensor-core GEMM with its operand splitting; mixed=2: the FP64 GEMM
@@ -193,6 +292,36 @@ def gemm_roofline(P, torch, b, reps=5, mixed=0):
     return ms, flops / (ms * 1e-3) / 1e12
 
 
+def emulated_kernel_ms(torch, b, reps=5):
+    """Duration of the emulated product's tensor-core kernel alone at b x b x
+    b (events recorded by bta_gemm_emulated_timed around that launch on its
+    stream), average over reps launches after two warm-up calls; operands are
+    symmetric-positive-definite-like blocks of the sweep's value range."""
+    import ctypes as C
+    from paper_2605_06392_gb300._capi import check, lib
+    A = torch.randn(b, b, dtype=torch.float64, device="cuda")
+    B = torch.randn(b, b, dtype=torch.float64, device="cuda")
+    Cm = torch.zeros(b, b, dtype=torch.float64, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    s = torch.cuda.current_stream()
+    out = []
+    for i in range(reps + 2):
+        ms = C.c_float(0.0)
+        check(lib().bta_gemm_emulated_timed(b, b, b, 1.0, C.c_void_p(A.data_ptr()), b, 0,
+                                            C.c_void_p(B.data_ptr()), b, 0, 0.0,
+                                            C.c_void_p(Cm.data_ptr()), b, 8,
+                                            C.c_void_p(st.data_ptr()), C.byref(ms),
+                                            C.c_void_p(s.cuda_stream)),
+              "bta_gemm_emulated_timed")
+        if i >= 2:
+            out.append(ms.value)
+    assert int(st.item()) == 0, "a bounded wait in the emulated product expired"
+    return float(np.mean(out))
+
+
+# ----------------------------------------------------------------------------
+# modes for manual runs
+# ----------------------------------------------------------------------------
 def run_batch(args, P, torch, workloads):
     """Independent coregionalised models of uneven block size (3 responses,
     grid side drawn from --grids, --batch-nt time blocks, d = 15), each at
@@ -254,8 +383,7 @@ def run_step(args, prob, model, theta, torch, stream):
            "low_memory": bool(args.low_memory),
            "precision": args.precision, "ms_per_step": ms, "f": f,
            "algorithmic_tflop_per_step": flops / 1e12,
-           "tflops_fp64_equivalent": flops / ms / 1e9,
-           "frac_of_fp64_peak": flops / ms / 1e9 / FP64_PEAK_TFLOPS}
+           "tflops_fp64_equivalent": flops / ms / 1e9}
     if args.step_fd:
         d = len(theta)
         pts = [theta] + [theta + s * 1e-3 * np.eye(d)[j] for j in range(d) for s in (1.0, -1.0)]
@@ -272,28 +400,91 @@ def run_step(args, prob, model, theta, torch, stream):
     print(json.dumps(out), flush=True)
 
 
+# ----------------------------------------------------------------------------
+# the side workload: the b = 1024 univariate model in all three precisions
+# ----------------------------------------------------------------------------
+def side_workload(P, torch, workloads, stream, steps, fp64_peak):
+    prob = workloads.make_problem(SIDE)
+    model = P.InlaModel(prob)
+    theta = prob.theta.copy()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pts = workloads.fd_stencil(theta, 1e-3)
+    out = {"workload": SIDE, "grid": "32x32", "b": prob.b, "nt": prob.nt, "a": prob.a,
+           "d": prob.d, "n_obs": prob.n_obs}
+    ref = None
+    for prec, name in ((0, "fp64"), (1, "mixed"), (2, "emulated_fp64")):
+        for _ in range(2):
+            f, g = model.value_and_grad(theta, precision=prec)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            f, g = model.value_and_grad(theta, precision=prec)
+        e1.record(stream)
+        e1.synchronize()
+        t = e0.elapsed_time(e1) / steps * 1e-3
+        x = model.mode().cpu().numpy()
+        parts = model.last_parts()
+        model.value_and_grad(pts[:1], grad=False, precision=prec)     # value-only graph
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fv, _ = model.value_and_grad(pts, grad=False, precision=prec)
+        e1.record(stream)
+        e1.synchronize()
+        t_fd = e0.elapsed_time(e1) * 1e-3
+        leg = {"ms_per_step": 1e3 * t, "gradients_per_s": 1.0 / t,
+               "fd_seconds_per_gradient": t_fd, "fd_evals": int(pts.shape[0]),
+               "speedup_ad_vs_fd": t_fd / t, "c_ad": t / (t_fd / pts.shape[0])}
+        if ref is None:
+            ref = (f, g, x, parts)
+            flops, _ = _flops_model(prob.b, prob.nt, prob.a)
+            leg.update({"achieved_tflops": flops / t / 1e12,
+                        "frac_of_fp64_peak": flops / t / 1e12 / fp64_peak,
+                        "max_rel_diff_fd_vs_ad": float(np.max(
+                            np.abs((fv[1::2] - fv[2::2]) / 2e-3 - g) /
+                            np.maximum(np.abs(g), 1.0)))})
+        else:
+            f0, g0, x0, p0 = ref
+            gscale = np.maximum(np.abs(g0), np.abs(p0["phase_a"]) + np.abs(p0["phase_b"]) +
+                                np.abs(p0["phase_c"]))
+            leg.update({"speedup_vs_fp64": out["fp64"]["ms_per_step"] / (1e3 * t),
+                        "rel_err_f": abs(f - f0) / abs(f0),
+                        "rel_err_x": float(np.max(np.abs(x - x0)) / np.max(np.abs(x0))),
+                        "rel_err_grad": [float(v) for v in np.abs(g - g0) / gscale],
+                        "reference": "FP64 GPU path of this run (itself within 1e-10 of the "
+                                     "FP64 oracle)"})
+        out[name] = leg
+    gms, gtf = gemm_roofline(P, torch, prob.b)
+    out["fp64_gemm_roofline"] = {"kernel": "gemm_f64_kernel at 1024 x 1024 x 1024",
+                                 "launch_ms": gms, "achieved": gtf, "peak": fp64_peak,
+                                 "unit": "TFLOP/s", "frac": gtf / fp64_peak}
+    model.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--fd-steps", type=int, default=2)
+    ap.add_argument("--no-fd", action="store_true", help="skip the headline FD leg")
+    ap.add_argument("--no-side", action="store_true", help="skip the b = 1024 side workload")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--side-steps", type=int, default=5)
     ap.add_argument("--nt", type=int, default=0,
                     help="override the number of time blocks (profiling a shorter copy of "
                          "the same model: identical per-block kernels)")
     ap.add_argument("--instances", type=int, default=31, help="batch mode: number of models")
     ap.add_argument("--grids", default="16,24,32", help="batch mode: grid sides drawn per model")
     ap.add_argument("--batch-nt", type=int, default=40, help="batch mode: time blocks per model")
-    ap.add_argument("--precision", type=int, default=0,
-                    help="batch / gemm / step modes: 0 FP64, 1 mixed, 2 emulated FP64")
+    ap.add_argument("--precision", type=int, default=PRECISION,
+                    help="0 FP64, 1 mixed, 2 emulated FP64 (headline and step/batch/gemm modes)")
     ap.add_argument("--mode", default="full", choices=["full", "gemm", "batch", "step"],
                     help="gemm: only the dominant kernel at the sweep's block shape "
                          "(the small case used for ncu captures); step: only the timed "
                          "value-and-gradient steps at --precision, inside the profiler range")
     ap.add_argument("--workload", default=WORKLOAD,
-                    help="step mode: the synthetic model (a name from workloads.WORKLOADS)")
+                    help="the synthetic model (a name from workloads.WORKLOADS)")
     ap.add_argument("--gemm-n", type=int, default=0,
                     help="gemm mode: the product's size n (n x n x n; default the block size)")
     ap.add_argument("--low-memory", action="store_true",
@@ -322,27 +513,35 @@ def main():
     import paper_2605_06392_gb300 as P
     import workloads
 
+    peaks = measured_peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    fp64_peak = fp64_peak_tflops(sms, peaks["sm_max_mhz"])
+
     if args.mode == "batch":
         return run_batch(args, P, torch, workloads)
     if args.mode == "gemm":
-        b = args.gemm_n or workloads.WORKLOADS[WORKLOAD]["nx"] * workloads.WORKLOADS[WORKLOAD]["ny"]
-        ms, tf = gemm_roofline(P, torch, b, reps=args.steps, mixed=args.precision)
-        name = {0: "gemm_f64_kernel", 1: "tc_gemm_tf32x3_kernel (+ split)",
-                2: "ozaki_gemm_kernel<8> (+ split)"}[args.precision]
+        b = args.gemm_n or 4800
+        if args.precision == 2:
+            ms = emulated_kernel_ms(torch, b, reps=args.steps)
+            tf = 2.0 * b ** 3 / (ms * 1e-3) / 1e12
+            name = "emulated product, tensor-core kernel alone"
+        else:
+            ms, tf = gemm_roofline(P, torch, b, reps=args.steps, mixed=args.precision)
+            name = {0: "gemm_f64_kernel", 1: "tc_gemm_tf32x3_kernel (+ split)"}[args.precision]
         print(json.dumps({"kernel": name, "shape": [b, b, b], "launch_ms": ms,
                           "tflops_fp64_equivalent": tf}), flush=True)
         return
 
-    prob = workloads.make_problem(args.workload if args.mode == "step" else WORKLOAD,
-                                  **({"nt": args.nt} if args.nt else {}))
+    prob = workloads.make_problem(args.workload, **({"nt": args.nt} if args.nt else {}))
     model = P.InlaModel(prob, low_memory=args.low_memory and args.mode == "step")
     theta = prob.theta.copy()
     stream = torch.cuda.current_stream()
     if args.mode == "step":
         return run_step(args, prob, model, theta, torch, stream)
-    # warm-up (also captures the CUDA graphs)
+    prec = args.precision
+    # warm-up (the first call also times the tile shapes and captures the graph)
     for _ in range(args.warmup):
-        f, g = model.value_and_grad(theta)
+        f, g = model.value_and_grad(theta, precision=prec)
     torch.cuda.synchronize()
 
     def barrier():
@@ -350,7 +549,8 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    # --- timed region: K gradient evaluations, device time by CUDA events
+    # --- timed region: K gradient evaluations, device time by CUDA events;
+    # each call copies theta in and f, grad out (pinned host buffers)
     clocks = ClockSampler()
     clocks.start()
     barrier()
@@ -361,7 +561,7 @@ def main():
     e0.record(stream)
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        f, g = model.value_and_grad(theta)          # host theta in, host f/grad out
+        f, g = model.value_and_grad(theta, precision=prec)
         host_times.append(time.perf_counter() - t0)
     e1.record(stream)
     e1.synchronize()
@@ -369,84 +569,47 @@ def main():
     barrier()
     clocks.stop()
     launches = model.kernel_launches() - k0
+    parts = model.last_parts()
     ms = e0.elapsed_time(e1) / args.steps
-    t_step = ms * 1e-3
-    t_step, t_host = reduce_replicas([t_step, float(np.mean(host_times))], dist, device="cuda")
+    t_step, t_host = reduce_replicas([ms * 1e-3, float(np.mean(host_times))], dist,
+                                     device="cuda")
     value = world / t_step
     e2e = world / t_host
 
-    # --- FD baseline: 2d+1 value-only evaluations per gradient, same GPU
-    pts = workloads.fd_stencil(theta, 1e-3)
-    t_fd, g_fd, t_fdb = float("nan"), np.full(prob.d, np.nan), float("nan")
-    if args.fd_steps > 0:
-        model.value_and_grad(pts[:2], grad=False)       # warm the value-only graph
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(args.fd_steps):
-            fv, _ = model.value_and_grad(pts, grad=False)
-        t_fd = (time.perf_counter() - t0) / args.fd_steps
-        g_fd = (fv[1::2] - fv[2::2]) / 2e-3
-        # batched: all 2d+1 evaluations swept together in the same launches
-        model.value_and_grad(pts, grad=False, concurrent=pts.shape[0])
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(args.fd_steps):
-            fvb, _ = model.value_and_grad(pts, grad=False, concurrent=pts.shape[0])
-        t_fdb = (time.perf_counter() - t0) / args.fd_steps
-
-    # --- mixed precision (tensor-core split-TF32 Schur products, FP64 diagonal
-    # factors / log-dets / refinement): time and error against the FP64 path
-    f, g = model.value_and_grad(theta)              # FP64 at theta (after the FD points)
-    x64 = model.mode().cpu().numpy()
-    parts64 = model.last_parts()
-    for _ in range(2):
-        fm, gm = model.value_and_grad(theta, precision=1)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(args.steps):
-        fm, gm = model.value_and_grad(theta, precision=1)
-    e1.record(stream)
-    e1.synchronize()
-    t_mixed = e0.elapsed_time(e1) / args.steps * 1e-3
-    xm = model.mode().cpu().numpy()
-    pm = model.last_parts()
-    gscale = np.maximum(np.abs(g), np.abs(parts64["phase_a"]) + np.abs(parts64["phase_b"]) +
-                        np.abs(parts64["phase_c"]))
-    mixed = {"ms_per_step": 1e3 * t_mixed, "gradients_per_s": 1.0 / t_mixed,
-             "speedup_vs_fp64": t_step / t_mixed,
-             "rel_err_f": abs(fm - f) / abs(f),
-             "rel_err_x": float(np.max(np.abs(xm - x64)) / np.max(np.abs(x64))),
-             "rel_err_grad": [float(v) for v in np.abs(gm - g) / gscale],
-             "reference": "FP64 GPU path of this run (itself within 1e-10 of the FP64 oracle)"}
-    del pm
-
-    # --- emulated FP64 (the b x b products from 8 BF16 slices on the tensor
-    # cores, everything else FP64): time and difference from the FP64 path
-    emulated = None
-    if prob.b <= 5120:
-        for _ in range(2):
-            fe, ge = model.value_and_grad(theta, precision=2)
+    # --- FD baseline: 2d+1 value-only evaluations of the same model, one pass
+    fd = None
+    if not args.no_fd:
+        pts = workloads.fd_stencil(theta, 1e-3)
+        model.value_and_grad(pts[:1], grad=False, precision=prec)   # value-only graph
         torch.cuda.synchronize()
         e0.record(stream)
-        for _ in range(args.steps):
-            fe, ge = model.value_and_grad(theta, precision=2)
+        t0 = time.perf_counter()
+        fv, _ = model.value_and_grad(pts, grad=False, precision=prec)
+        t_fd_host = time.perf_counter() - t0
         e1.record(stream)
         e1.synchronize()
-        t_emu = e0.elapsed_time(e1) / args.steps * 1e-3
-        xe = model.mode().cpu().numpy()
-        emulated = {"ms_per_step": 1e3 * t_emu, "gradients_per_s": 1.0 / t_emu,
-                    "speedup_vs_fp64": t_step / t_emu,
-                    "rel_err_f": abs(fe - f) / abs(f),
-                    "rel_err_x": float(np.max(np.abs(xe - x64)) / np.max(np.abs(x64))),
-                    "rel_err_grad": [float(v) for v in np.abs(ge - g) / gscale],
-                    "reference": "FP64 GPU path of this run"}
+        t_fd = e0.elapsed_time(e1) * 1e-3
+        g_fd = (fv[1::2] - fv[2::2]) / 2e-3
+        fd = {"seconds_per_gradient": t_fd, "host_seconds": t_fd_host,
+              "evals_per_gradient": int(pts.shape[0]), "gradients_per_s": 1.0 / t_fd,
+              "speedup_ad_vs_fd": t_fd / t_step, "c_ad": t_step / (t_fd / pts.shape[0]),
+              "precision": "emulated f64" if prec == 2 else {0: "f64", 1: "mixed"}[prec],
+              "max_rel_diff_fd_vs_ad": float(np.max(np.abs(g_fd - g) /
+                                                    np.maximum(np.abs(g), 1.0)))}
 
-    # --- dominant kernel roofline
-    gemm_ms, gemm_tf = gemm_roofline(P, torch, prob.b)
-
-    parts = parts64          # the FP64 evaluation at theta
+    # --- dominant kernel: the emulated product's tensor-core kernel at the
+    # sweep's block shape (b x b x b), timed alone right after the steps
+    b = prob.b
+    kms = emulated_kernel_ms(torch, min(b, 5120))
+    kb = min(b, 5120)
+    bf16_flop = PAIRS * 2.0 * float(kb) ** 3
+    achieved = bf16_flop / (kms * 1e-3) / 1e12
     flops_grad, flops_val = _flops_model(prob.b, prob.nt, prob.a)
     step_tf = flops_grad / t_step / 1e12
+    ceiling = peaks["bf16_tflops_sustained"] / PAIRS      # FP64-equivalent tensor ceiling
+    ld_closed = spectral_logdet_prior(prob)
+    side = None if args.no_side else side_workload(P, torch, workloads, stream, args.side_steps,
+                                                   fp64_peak)
     out = None
     if rank == 0:
         cpu = None if args.no_cpu else cpu_baseline()
@@ -457,32 +620,41 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD if not args.nt else f"{WORKLOAD}_nt{args.nt}",
-                       "grid": "32x32", "b": prob.b, "ld": model.ld,
+            "config": {"workload": args.workload if not args.nt else f"{args.workload}_nt{args.nt}",
+                       "grid": f"{prob.k} x {prob.nx}x{prob.ny}", "b": prob.b, "ld": model.ld,
                        "nt": prob.nt, "a": prob.a, "d": prob.d, "n_obs": prob.n_obs,
-                       "l2": "working set 1.7 GB > L2, no flush", "parallelism": "replicas"},
+                       "arithmetic": ("FP64 results; every b x b product emulated to FP64 "
+                                      "accuracy from 8 BF16 slices on tcgen05 (36 slice "
+                                      "products), diagonal-block leaves, log-dets, arrow, tip "
+                                      "and reductions on the FP64 pipe") if prec == 2 else
+                                     {0: "FP64", 1: "mixed (split TF32)"}[prec],
+                       "l2": f"working set {2 * prob.nt * model.ld ** 2 * 8 / 1e9:.0f} GB > "
+                             "L2, no flush", "parallelism": "replicas"},
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 8 * prob.d,
                     "d2h_bytes_per_step": 8 * (1 + prob.d + 8 + 4 * prob.d)},
             "gpu_launches": int(launches),
-            "fd_baseline": {"seconds_per_gradient": t_fd, "evals_per_gradient": pts.shape[0],
-                            "gradients_per_s": 1.0 / t_fd,
-                            "speedup_ad_vs_fd": t_fd / t_step,
-                            "c_ad": t_step / (t_fd / pts.shape[0]),
-                            "batched_seconds_per_gradient": t_fdb,
-                            "speedup_ad_vs_batched_fd": t_fdb / t_step,
-                            "max_rel_diff_fd_vs_ad": float(np.max(np.abs(g_fd - g) /
-                                                                  np.maximum(np.abs(g), 1.0)))},
-            "mixed_precision": mixed,
-            "emulated_fp64": emulated,
-            "fp64_step": {"algorithmic_tflop_per_step": flops_grad / 1e12,
-                          "achieved_tflops": step_tf, "frac_of_peak": step_tf / FP64_PEAK_TFLOPS},
-            "roofline": {"bound": "alu", "kernel": "gemm_f64_kernel<32,32> at b x b x b",
-                         "achieved": gemm_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": gemm_tf / FP64_PEAK_TFLOPS, "traffic": 16.8e6,
-                         "traffic_source": "ncu dram__bytes_read+write per launch, "
-                                           "profiles/gemm_f64_block1024.md",
-                         "launch_ms": gemm_ms,
-                         "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz"},
+            "fd_baseline": fd,
+            "step": {"algorithmic_fp64_tflop": flops_grad / 1e12,
+                     "fp64_equivalent_tflops": step_tf,
+                     "frac_of_emulated_ceiling": step_tf / ceiling,
+                     "emulated_ceiling_tflops": ceiling,
+                     "ceiling_source": "measured sustained BF16 rate / 36 slice products",
+                     "frac_of_fp64_pipe_peak": step_tf / fp64_peak},
+            "roofline": {"bound": "tensor", "kernel": f"emulated product tensor-core kernel at "
+                                                      f"{kb} x {kb} x {kb} (BF16 slices)",
+                         "achieved": achieved, "peak": peaks["bf16_tflops_sustained"],
+                         "unit": "TFLOP/s", "frac": achieved / peaks["bf16_tflops_sustained"],
+                         "traffic": None,
+                         "launch_ms": kms,
+                         "algorithmic": f"36 x 2 x {kb}^3 BF16 flop per launch",
+                         "fp64_equivalent_tflops": 2.0 * float(kb) ** 3 / (kms * 1e-3) / 1e12,
+                         "frac_of_burst": achieved / peaks["bf16_tflops"],
+                         "peak_source": f"{peaks['source']} bf16_tflops_sustained (the kernel "
+                                        f"runs inside a {t_step:.0f}-s step)"},
+            "checks": {"logdet_p": parts["logdet_p"], "logdet_p_closed_form": ld_closed,
+                       "logdet_p_rel_err": abs(parts["logdet_p"] - ld_closed) / abs(ld_closed),
+                       "fail_c": parts["fail_c"], "fail_p": parts["fail_p"]},
+            "side_workload": side,
             "clocks": clocks.summary(),
             "result": {"f": f, "grad": [float(v) for v in g], "logdet_c": parts["logdet_c"],
                        "logdet_p": parts["logdet_p"]},

@@ -344,6 +344,20 @@ bta_status bta_gemm_emulated(int32_t M, int32_t N, int32_t K, double alpha, cons
                              int32_t slices, int32_t* status, cudaStream_t stream);
 
 /*
+ * bta_gemm_emulated_timed -- bta_gemm_emulated (same arguments and result)
+ * that also writes to kernel_ms (host float) the duration of its tensor-core
+ * product kernel alone, from CUDA events recorded on the stream around that
+ * launch (the exponent, split and compose kernels excluded): the measurement
+ * behind the emulated product's roofline.  Synchronises the stream.  The
+ * paper has no counterpart.
+ */
+bta_status bta_gemm_emulated_timed(int32_t M, int32_t N, int32_t K, double alpha,
+                                   const double* A, int32_t lda, int32_t transA, const double* B,
+                                   int32_t ldb, int32_t transB, double beta, double* C,
+                                   int32_t ldc, int32_t slices, int32_t* status,
+                                   float* kernel_ms, cudaStream_t stream);
+
+/*
  * inla_grid_stencil -- spatial base matrices of an nx x ny grid model
  * (Section II-A): Cm = I, G = 5-point graph Laplacian with natural boundary,
  * GG = G G, all on GG's 13-point pattern, CSR with sorted columns (host

@@ -92,6 +92,11 @@ SIGNATURES = {
                                     C.c_int32, C.c_int32, C.c_void_p, C.c_int32, C.c_int32,
                                     C.c_double, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
                                     C.c_void_p]),
+    "bta_gemm_emulated_timed": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_double,
+                                          C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
+                                          C.c_int32, C.c_int32, C.c_double, C.c_void_p,
+                                          C.c_int32, C.c_int32, C.c_void_p,
+                                          C.POINTER(C.c_float), C.c_void_p]),
     "inla_grid_stencil": (C.c_int, [C.c_int32, C.c_int32, C.POINTER(C.c_int32), C.c_void_p,
                                     C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
 }

@@ -761,6 +761,38 @@ bta_status bta_gemm_emulated(int32_t M, int32_t N, int32_t K, double alpha, cons
   return st;
 }
 
+bta_status bta_gemm_emulated_timed(int32_t M, int32_t N, int32_t K, double alpha,
+                                   const double* A, int32_t lda, int32_t transA, const double* B,
+                                   int32_t ldb, int32_t transB, double beta, double* Cm,
+                                   int32_t ldc, int32_t slices, int32_t* status,
+                                   float* kernel_ms, cudaStream_t stream) {
+  if (M < 1 || N < 1 || K < 1 || K > 5120 || !A || !B || !Cm || slices < 6 || slices > 8 ||
+      !kernel_ms)
+    return BTA_ERR_ARG;
+  Gemm g;
+  g.M = M; g.N = N; g.K = K; g.alpha = alpha; g.beta = beta;
+  g.A = A; g.lda = lda; g.transA = transA ? 1 : 0;
+  g.B = B; g.ldb = ldb; g.transB = transB ? 1 : 0;
+  g.C = Cm; g.ldc = ldc; g.Cin = Cm; g.ldcin = ldc;
+  cudaEvent_t marks[2] = {nullptr, nullptr};
+  BTA_CUDA_TRY(cudaEventCreate(&marks[0]));
+  BTA_CUDA_TRY(cudaEventCreate(&marks[1]));
+  void* ws = nullptr;
+  bta_status st = BTA_OK;
+  if (cudaMallocAsync(&ws, ozaki_ws_bytes(M, N, K, slices), stream) != cudaSuccess) {
+    cudaGetLastError();
+    st = BTA_ERR_NOMEM;
+  }
+  if (st == BTA_OK) st = ozaki_gemm(g, ws, status, slices, stream, marks);
+  if (ws) cudaFreeAsync(ws, stream);
+  if (st == BTA_OK && cudaEventSynchronize(marks[1]) == cudaSuccess &&
+      cudaEventElapsedTime(kernel_ms, marks[0], marks[1]) != cudaSuccess)
+    st = BTA_ERR_CUDA;
+  cudaEventDestroy(marks[0]);
+  cudaEventDestroy(marks[1]);
+  return st;
+}
+
 bta_status inla_batch_create(inla_model* const* models, int32_t count, inla_batch** out) {
   if (!models || !out || count < 1) return BTA_ERR_ARG;
   *out = nullptr;

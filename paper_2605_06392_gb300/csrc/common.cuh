@@ -157,7 +157,9 @@ bta_status tc_gemm_mixed(const Gemm& g, void* ws, int32_t* status, cudaStream_t 
 size_t tc_gemm_ws_bytes(int M, int N, int K);
 // FP64 GEMM emulated on BF16 tensor cores with `slices` (6..8) base-128
 // digits per operand (ozaki_gemm.cu); single problem, K <= 5120.
-bta_status ozaki_gemm(const Gemm& g, void* ws, int32_t* status, int slices, cudaStream_t s);
+// marks (optional): events recorded around the tensor-core product kernel.
+bta_status ozaki_gemm(const Gemm& g, void* ws, int32_t* status, int slices, cudaStream_t s,
+                      const cudaEvent_t* marks = nullptr);
 size_t ozaki_ws_bytes(int M, int N, int K, int slices);
 bool ozaki_supported(const Gemm& g);
 

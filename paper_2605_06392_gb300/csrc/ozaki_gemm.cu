@@ -457,8 +457,23 @@ constexpr uint32_t kQIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(QN
 __host__ __device__ constexpr int q_a0(int P) { return P == 3 ? 4 : 0; }
 __host__ __device__ constexpr int q_b0(int P) { return P == 1 ? 4 : 0; }
 
-// MMA of A slot I and B slot LL in sub-pass P for the 16-wide K step KK.
-template <int P, int I, int LL, int KK>
+// CTA-pair variant (ozaki_gemm_pair_kernel below): M = 256 over two CTAs,
+// each holding 128 A rows and 64 of the 128 B columns (4 KB a B slot).
+constexpr int kPM = 256;
+constexpr int kPBRows = 64;
+constexpr int kPBTile = kPBRows * OK16 * 2;       // 4 KB
+constexpr int kPStage = 4 * kQTile + 4 * kPBTile;  // 48 KB
+constexpr int kPStages = 4;
+// ring, barriers, and 8 KB of slack past the ring: every operand read an MMA
+// can make from a slot stays inside the allocation
+constexpr int kPSmem = kPStages * kPStage + 1024 + 256 + 8192;
+constexpr uint32_t kPIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(QN >> 3) << 17) |
+                             ((uint32_t)(kPM >> 4) << 24);
+
+// MMA of A slot I and B slot LL in sub-pass P for the 16-wide K step KK:
+// one CTA (PAIR = false, M = 128) or a CTA pair (PAIR = true, M = 256, issued
+// by the pair's leader; the descriptors name the same offsets in both CTAs).
+template <bool PAIR, int P, int I, int LL, int KK>
 __device__ __forceinline__ void q_pair(uint32_t tmem, uint64_t dst, uint32_t first,
                                        uint32_t leader) {
   constexpr int L = q_a0(P) + I + q_b0(P) + LL + 2;   // level
@@ -469,15 +484,28 @@ __device__ __forceinline__ void q_pair(uint32_t tmem, uint64_t dst, uint32_t fir
     constexpr bool kMayOpen = KK == 0 && I == 0 && (P == 0 || (P == 1 && L <= 8));
     const uint32_t accumulate = kMayOpen ? (first ? 0u : 1u) : 1u;
     constexpr unsigned long long kAo = (unsigned long long)(I * kQTile + KK * 32) >> 4;
-    constexpr unsigned long long kBo = (unsigned long long)((4 + LL) * kQTile + KK * 32) >> 4;
-    asm volatile(
-        "{\n .reg .b64 da, db;\n .reg .pred p, e;\n"
-        " add.s64 da, %1, %2;\n add.s64 db, %1, %3;\n"
-        " setp.ne.b32 p, %5, 0;\n setp.ne.b32 e, %6, 0;\n"
-        " @e tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %4, p;\n}\n" ::"r"(
-            tmem + (uint32_t)(kAcc * QN)),
-        "l"(dst), "n"(kAo), "n"(kBo), "r"(kQIdesc), "r"(accumulate), "r"(leader)
-        : "memory");
+    constexpr unsigned long long kBo =
+        PAIR ? (unsigned long long)(4 * kQTile + LL * kPBTile + KK * 32) >> 4
+             : (unsigned long long)((4 + LL) * kQTile + KK * 32) >> 4;
+    if constexpr (PAIR) {
+      asm volatile(
+          "{\n .reg .b64 da, db;\n .reg .pred p, e;\n"
+          " add.s64 da, %1, %2;\n add.s64 db, %1, %3;\n"
+          " setp.ne.b32 p, %5, 0;\n setp.ne.b32 e, %6, 0;\n"
+          " @e tcgen05.mma.cta_group::2.kind::f16 [%0], da, db, %4, p;\n}\n" ::"r"(
+              tmem + (uint32_t)(kAcc * QN)),
+          "l"(dst), "n"(kAo), "n"(kBo), "r"(kPIdesc), "r"(accumulate), "r"(leader)
+          : "memory");
+    } else {
+      asm volatile(
+          "{\n .reg .b64 da, db;\n .reg .pred p, e;\n"
+          " add.s64 da, %1, %2;\n add.s64 db, %1, %3;\n"
+          " setp.ne.b32 p, %5, 0;\n setp.ne.b32 e, %6, 0;\n"
+          " @e tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %4, p;\n}\n" ::"r"(
+              tmem + (uint32_t)(kAcc * QN)),
+          "l"(dst), "n"(kAo), "n"(kBo), "r"(kQIdesc), "r"(accumulate), "r"(leader)
+          : "memory");
+    }
   }
 }
 
@@ -486,32 +514,32 @@ __device__ __forceinline__ void q_pair(uint32_t tmem, uint64_t dst, uint32_t fir
 // MMAs accumulate into the same TMEM accumulator.  A level's first MMA is
 // its pair with A slot 0 at K step 0 (present in every level of P0 and P1),
 // which opens the accumulator in the first slab of a chunk.
-template <int P, int L, int I>
+template <bool PAIR, int P, int L, int I>
 __device__ __forceinline__ void q_level(uint32_t tmem, uint64_t dst, uint32_t first,
                                         uint32_t leader) {
   if constexpr (I < 4) {
     constexpr int LL = L - 2 - q_a0(P) - q_b0(P) - I;
     if constexpr (LL >= 0 && LL < 4) {
-      q_pair<P, I, LL, 0>(tmem, dst, first, leader);
-      q_pair<P, I, LL, 1>(tmem, dst, first, leader);
+      q_pair<PAIR, P, I, LL, 0>(tmem, dst, first, leader);
+      q_pair<PAIR, P, I, LL, 1>(tmem, dst, first, leader);
     }
-    q_level<P, L, I + 1>(tmem, dst, first, leader);
+    q_level<PAIR, P, L, I + 1>(tmem, dst, first, leader);
   }
 }
 
-template <int P, int L>
+template <bool PAIR, int P, int L>
 __device__ __forceinline__ void q_levels(uint32_t tmem, uint64_t dst, uint32_t first,
                                          uint32_t leader) {
   if constexpr (L <= 9) {
-    q_level<P, L, 0>(tmem, dst, first, leader);
-    q_levels<P, L + 1>(tmem, dst, first, leader);
+    q_level<PAIR, P, L, 0>(tmem, dst, first, leader);
+    q_levels<PAIR, P, L + 1>(tmem, dst, first, leader);
   }
 }
 
-template <int P>
+template <bool PAIR, int P>
 __device__ __forceinline__ void q_slab(uint32_t tmem, uint64_t dst, uint32_t first,
                                        uint32_t leader) {
-  q_levels<P, 2>(tmem, dst, first, leader);
+  q_levels<PAIR, P, 2>(tmem, dst, first, leader);
 }
 
 // OR of v over the 512 threads of warps 0-15 (named barrier 1).
@@ -530,9 +558,28 @@ struct OzqArgs {
   int Mp, Np, Bp, nk, splits;   // nk: 32-wide K slabs; Bp: rows per B slice in its array
   int group;                             // tile rows per group of the launch order
   int out_lower;
+  int tri_a, tri_b;     // triangle of op(A) / op(B) (Tri): their zero K ranges are skipped
   long long* partial;   // [splits][Np][Mp] integer sums, units 2^-35 of level 2
   int32_t* status;
 };
+
+// The 32-wide K slabs [kb, ke) of a tile with output rows m0 .. m0 + rows - 1
+// and columns n0 .. n0 + cols - 1 on which op(A) and op(B) can be nonzero: a
+// lower op(A) has a_mk = 0 for k > m, an upper one for k < m; a lower op(B)
+// has b_kn = 0 for k < n, an upper one for k > n.  The slices hold exact zeros
+// there (the split masks the triangles), so leaving those slabs out changes
+// no level sum.  Split z of `splits` takes its share of [kb, ke).
+__device__ __forceinline__ void tile_slabs(const OzqArgs& g, int m0, int rows, int n0, int cols,
+                                           int z, int& ks0, int& ks1) {
+  int kb = 0, ke = g.nk;
+  if (g.tri_a == TRI_LOWER) ke = min(ke, (m0 + rows + OK16 - 1) / OK16);
+  if (g.tri_a == TRI_UPPER) kb = max(kb, m0 / OK16);
+  if (g.tri_b == TRI_LOWER) kb = max(kb, n0 / OK16);
+  if (g.tri_b == TRI_UPPER) ke = min(ke, (n0 + cols + OK16 - 1) / OK16);
+  if (ke < kb) ke = kb;
+  ks0 = kb + (int)((int64_t)z * (ke - kb) / g.splits);
+  ks1 = kb + (int)((int64_t)(z + 1) * (ke - kb) / g.splits);
+}
 
 // 8 consecutive fp32 columns of this thread's TMEM lane.
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
@@ -562,8 +609,8 @@ __global__ void __launch_bounds__(kQThreads, 1)
   if (g.out_lower && n0 > m0 + OM - 1) return;   // whole CTA exits before any set-up
   // this CTA's slabs of K: split z of `splits` near-equal ranges, taken in
   // chunks of at most 16 slabs (512 of K: the exactness limit of a level sum)
-  const int ks0 = (int)((int64_t)z * g.nk / g.splits);
-  const int ks1 = (int)((int64_t)(z + 1) * g.nk / g.splits);
+  int ks0, ks1;
+  tile_slabs(g, m0, OM, n0, QN, z, ks0, ks1);
   const int nc = (ks1 - ks0 + kChunkSlabs - 1) / kChunkSlabs;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>(
@@ -664,10 +711,10 @@ __global__ void __launch_bounds__(kQThreads, 1)
           // completion already orders it before the MMAs that read it)
           const uint64_t dst = dbase + (uint64_t)((s * kQStage) >> 4);
           const uint32_t first = kt == kt0;
-          if (P == 0) q_slab<0>(tmem, dst, first, leader);
-          else if (P == 1) q_slab<1>(tmem, dst, first, leader);
-          else if (P == 2) q_slab<2>(tmem, dst, first, leader);
-          else q_slab<3>(tmem, dst, first, leader);
+          if (P == 0) q_slab<false, 0>(tmem, dst, first, leader);
+          else if (P == 1) q_slab<false, 1>(tmem, dst, first, leader);
+          else if (P == 2) q_slab<false, 2>(tmem, dst, first, leader);
+          else q_slab<false, 3>(tmem, dst, first, leader);
           mma_commit_if(smem_u32(&bars[kEmpty + s]), leader);   // slab free once these finish
           if (leader) *(volatile int*)&s_consumed = r + 1;
           __syncwarp();
@@ -754,6 +801,353 @@ __global__ void __launch_bounds__(kQThreads, 1)
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512)
+                 : "memory");
+  }
+}
+
+// ---- 256 x 128 tiles on a CTA pair (S = 8) ---------------------------------
+//
+// The products of ozaki_gemm128_kernel with M = 256 MMAs over a pair of CTAs
+// on two SMs (a thread-block cluster of 2, tcgen05 cta_group::2).  CTA r of
+// the pair loads rows r*128 .. r*128+127 of the pair's A rows and B rows
+// (columns of op(B)) r*64 .. r*64+63 of its 128; one MMA, issued by the
+// leader (r = 0), reads both CTAs' shared memory and accumulates each CTA's
+// 128 output rows in that CTA's tensor memory.  Per 128 x 128 x 16 of work an
+// SM then reads 4 KB of A and 2 KB of B (8 KB in the one-CTA kernel) and its
+// TMA writes 48 KB per slab (64 KB), which relieves the shared-memory port
+// that bounds the one-CTA kernel.  Sub-passes, accumulator sets, drains and
+// integer sums are those of ozaki_gemm128_kernel, per CTA.
+//
+// Across the pair: each CTA's loads complete on its own `loaded` barrier, so
+// each can account for its own copies; the peer's warp 17 relays every
+// completed slab to the leader's `peer` barrier (a remote arrive), and the
+// leader's MMA warp starts a slab once both halves are in.  The leader's
+// commits arrive on both CTAs' `empty` and `accfull` barriers (multicast);
+// each CTA's drain warps, when done with a set, arrive once on the leader's
+// `accempty`.  Before releasing tensor memory the two CTAs exchange `done`
+// arrivals, so neither deallocates or exits while the other may still touch
+// its shared or tensor memory.  Every wait is bounded; on expiry a CTA records
+// BTA_ERR_TIMEOUT, stops issuing, waits (bounded) for its own loads and MMAs
+// and still takes part in the exchange.
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// The shared::cluster address of the same shared-memory offset in CTA `rank`.
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t local, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+  return r;
+}
+
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t caddr) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(caddr)
+               : "memory");
+}
+
+// Bounded wait with cluster-scope acquire (the barrier receives arrivals from
+// the peer CTA or the leader's tensor-core commits).
+__device__ __forceinline__ bool mbar_wait_cl(uint32_t addr, uint32_t parity, long long limit) {
+  for (long long it = 0; it < limit; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ bool warp_wait_cl(uint32_t addr, uint32_t parity, int lane) {
+  int ok = 0;
+  if (lane == 0) ok = mbar_wait_cl(addr, parity, kOzWaitLimit) ? 1 : 0;
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+// Commit of the leader's pair MMAs: arrive on the barrier at this offset in
+// both CTAs once they complete.
+__device__ __forceinline__ void pair_commit_both(uint32_t mbar, uint32_t leader) {
+  const uint16_t mask = 3;
+  asm volatile(
+      "{\n .reg .pred e;\n setp.ne.b32 e, %1, 0;\n"
+      " @e tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+      " [%0], %2;\n}\n" ::"r"(mbar),
+      "r"(leader), "h"(mask)
+      : "memory");
+}
+
+// ... on the leader's barrier only.
+__device__ __forceinline__ void pair_commit_own(uint32_t mbar, uint32_t leader) {
+  asm volatile(
+      "{\n .reg .pred e;\n setp.ne.b32 e, %1, 0;\n"
+      " @e tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];\n}\n" ::"r"(
+          mbar),
+      "r"(leader)
+      : "memory");
+}
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kQThreads, 1)
+    ozaki_gemm_pair_kernel(const __grid_constant__ CUtensorMap mA,
+                           const __grid_constant__ CUtensorMap mB, OzqArgs g) {
+  // Pair-tile order: groups of `group` pair rows, column by column inside a
+  // group (as ozaki_gemm128_kernel, in units of 256 x 128 tiles).
+  const uint32_t rank = cluster_rank();
+  const int pt = (int)blockIdx.x >> 1;
+  const int mt_all = g.Mp / kPM, nt_all = g.Np / QN;
+  const int grp = pt / (g.group * nt_all);
+  const int gm = min(g.group, mt_all - grp * g.group);
+  const int in = pt - grp * g.group * nt_all;
+  const int pm0 = (grp * g.group + in % gm) * kPM, n0 = (in / gm) * QN, z = blockIdx.z;
+  // the same decision in both CTAs of the pair: the pair exits before any set-up
+  if (g.out_lower && n0 > pm0 + kPM - 1) return;
+  const int m0 = pm0 + (int)rank * OM;                 // this CTA's A rows / output rows
+  const int nb0 = n0 + (int)rank * kPBRows;            // this CTA's B rows (columns of C)
+  // the pair's K range (the same in both CTAs: it depends on the pair tile)
+  int ks0, ks1;
+  tile_slabs(g, pm0, kPM, n0, QN, z, ks0, ks1);
+  const int nc = (ks1 - ks0 + kChunkSlabs - 1) / kChunkSlabs;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kPStages * kPStage);
+  const int kLoaded = 0, kPeer = kPStages, kEmpty = 2 * kPStages, kAccFull = 3 * kPStages,
+            kAccEmpty = 3 * kPStages + 1, kFinal = 3 * kPStages + 2, kDone = 3 * kPStages + 3;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3 * kPStages + 4);
+  __shared__ int s_abort, s_issued, s_waited;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kPStages; ++s) {
+      mbar_init(smem_u32(&bars[kLoaded + s]), 1);
+      mbar_init(smem_u32(&bars[kPeer + s]), 1);
+      mbar_init(smem_u32(&bars[kEmpty + s]), 1);
+    }
+    mbar_init(smem_u32(&bars[kAccFull]), 1);
+    mbar_init(smem_u32(&bars[kAccEmpty]), 2);   // one arrival per CTA of the pair
+    mbar_init(smem_u32(&bars[kFinal]), 1);
+    mbar_init(smem_u32(&bars[kDone]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_abort = 0;
+    s_issued = 0;
+    s_waited = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  // both CTAs' barriers and tensor memory are set up before either touches the other's
+  asm volatile("barrier.cluster.arrive.release.aligned;\n"
+               "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 16) {
+    // ---- TMA producer (both CTAs): this CTA's halves of every slab
+    const uint32_t leader = lane == 0;
+    int r = 0;
+    bool stop = false;
+    for (int c = 0; c < nc && !stop; ++c) {
+      const int kt0 = ks0 + c * kChunkSlabs, kt1 = min(ks1, kt0 + kChunkSlabs);
+      for (int P = 0; P < kQPasses && !stop; ++P) {
+        const int aj0 = q_a0(P), bl0 = q_b0(P);
+        for (int kt = kt0; kt < kt1; ++kt, ++r) {
+          const int s = r % kPStages;
+          if (r >= kPStages && !warp_wait_cl(smem_u32(&bars[kEmpty + s]),
+                                             (uint32_t)((r / kPStages - 1) & 1), lane)) {
+            if (leader) atomicExch(&s_abort, 1);
+            stop = true;
+            break;
+          }
+          if (warp_flag(&s_abort, lane)) {
+            stop = true;
+            break;
+          }
+          if (leader) {
+            const uint32_t full = smem_u32(&bars[kLoaded + s]);
+            mbar_expect_tx(full, (uint32_t)kPStage);
+            uint8_t* st = smem + s * kPStage;
+            const int k0 = kt * OK16;
+            for (int i = 0; i < 4; ++i)
+              tma_load_2d(smem_u32(st + i * kQTile), &mA, full, k0, (aj0 + i) * g.Mp + m0);
+            for (int l = 0; l < 4; ++l)
+              tma_load_2d(smem_u32(st + 4 * kQTile + l * kPBTile), &mB, full, k0,
+                          (bl0 + l) * g.Bp + nb0);
+            *(volatile int*)&s_issued = r + 1;
+          }
+          __syncwarp();
+        }
+      }
+    }
+  } else if (warp == 17 && rank != 0) {
+    // ---- relay (peer CTA): each slab of this CTA in place -> the leader's `peer`
+    int r = 0;
+    bool stop = false;
+    for (int c = 0; c < nc && !stop; ++c) {
+      const int kt0 = ks0 + c * kChunkSlabs, kt1 = min(ks1, kt0 + kChunkSlabs);
+      for (int P = 0; P < kQPasses && !stop; ++P) {
+        for (int kt = kt0; kt < kt1; ++kt, ++r) {
+          const int s = r % kPStages;
+          if (warp_flag(&s_abort, lane) ||
+              !warp_wait(smem_u32(&bars[kLoaded + s]), (uint32_t)((r / kPStages) & 1), lane)) {
+            if (lane == 0) atomicExch(&s_abort, 1);
+            stop = true;
+            break;
+          }
+          if (lane == 0) {
+            mbar_arrive_remote(cluster_addr(smem_u32(&bars[kPeer + s]), 0));
+            *(volatile int*)&s_waited = r + 1;
+          }
+          __syncwarp();
+        }
+      }
+    }
+  } else if (warp == 17) {
+    // ---- MMA issuer (leader CTA): the whole warp runs the loop, lane 0 issues
+    const uint32_t leader = lane == 0;
+    const uint64_t dbase = sdesc64(smem_u32(smem));
+    bool stop = false;
+    int r = 0, e = 0;   // slabs consumed, accumulator sets handed to the drains
+    for (int c = 0; c < nc && !stop; ++c) {
+      const int kt0 = ks0 + c * kChunkSlabs, kt1 = min(ks1, kt0 + kChunkSlabs);
+      for (int P = 0; P < kQPasses && !stop; ++P) {
+        // P0 and P1 open an accumulator set: wait until both CTAs drained the last one
+        if (P <= 1 && e > 0 &&
+            !warp_wait_cl(smem_u32(&bars[kAccEmpty]), (uint32_t)((e - 1) & 1), lane)) {
+          stop = true;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        for (int kt = kt0; kt < kt1; ++kt, ++r) {
+          const int s = r % kPStages;
+          const uint32_t par = (uint32_t)((r / kPStages) & 1);
+          if (warp_flag(&s_abort, lane) || !warp_wait(smem_u32(&bars[kLoaded + s]), par, lane)) {
+            stop = true;
+            break;
+          }
+          if (leader) *(volatile int*)&s_waited = r + 1;
+          if (!warp_wait_cl(smem_u32(&bars[kPeer + s]), par, lane)) {
+            stop = true;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint64_t dst = dbase + (uint64_t)((s * kPStage) >> 4);
+          const uint32_t first = kt == kt0;
+          if (P == 0) q_slab<true, 0>(tmem, dst, first, leader);
+          else if (P == 1) q_slab<true, 1>(tmem, dst, first, leader);
+          else if (P == 2) q_slab<true, 2>(tmem, dst, first, leader);
+          else q_slab<true, 3>(tmem, dst, first, leader);
+          pair_commit_both(smem_u32(&bars[kEmpty + s]), leader);   // both halves free
+          __syncwarp();
+        }
+        if (!stop && (P == 0 || P == kQPasses - 1)) {
+          pair_commit_both(smem_u32(&bars[kAccFull]), leader);     // this set's sums ready
+          ++e;
+        }
+      }
+    }
+    if (stop) {
+      if (leader) atomicExch(&s_abort, 1);
+      // wait (bounded) for the MMAs this warp issued before leaving
+      pair_commit_own(smem_u32(&bars[kFinal]), leader);
+      warp_wait(smem_u32(&bars[kFinal]), 0, lane);
+    }
+  } else if (warp < 16) {
+    // ---- warps 0-15 (both CTAs): thread = output row (TMEM lane) x 32
+    // columns; the tile's integer sums (units 2^-35 of the level-2 unit) stay
+    // in registers
+    const uint32_t lane_off = (uint32_t)((warp & 3) * 32) << 16;
+    const int row = (warp & 3) * 32 + lane, col0 = (warp >> 2) * 32;
+    const uint32_t acc_empty = cluster_addr(smem_u32(&bars[kAccEmpty]), 0);
+    long long acc[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) acc[q] = 0ll;
+    int failed = 0, e = 0;
+    for (int c = 0; c < nc && !failed; ++c) {
+      for (int set = 0; set < 2; ++set, ++e) {
+        const bool ok = mbar_wait_cl(smem_u32(&bars[kAccFull]), (uint32_t)(e & 1), kOzWaitLimit);
+        if (bar_or_512(!ok || *(volatile int*)&s_abort)) {
+          failed = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        float v[8];
+        if (set == 0) {
+          // levels 2..5
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            const float up = __int_as_float((127 + 7 * a) << 23);
+            const long long sc = 1ll << (7 * (5 - a));
+#pragma unroll
+            for (int hh = 0; hh < 4; ++hh) {
+              tmem_ld8(tmem + lane_off + (uint32_t)(a * QN + col0 + 8 * hh), v);
+#pragma unroll
+              for (int q = 0; q < 8; ++q)
+                acc[8 * hh + q] += (long long)__float2int_rn(v[q] * up) * sc;
+            }
+          }
+        } else {
+#pragma unroll
+          for (int hh = 0; hh < 4; ++hh) {
+            tmem_ld8(tmem + lane_off + (uint32_t)(0 * QN + col0 + 8 * hh), v);   // level 6
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+              acc[8 * hh + q] += (long long)__float2int_rn(v[q] * 268435456.0f) * 128ll;
+            tmem_ld8(tmem + lane_off + (uint32_t)(1 * QN + col0 + 8 * hh), v);   // level 7
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+              acc[8 * hh + q] += (long long)__float2int_rn(v[q] * 34359738368.0f);
+            tmem_ld8(tmem + lane_off + (uint32_t)(2 * QN + col0 + 8 * hh), v);   // levels 8, 9
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc[8 * hh + q] += __float2ll_rn(v[q] * 34359738368.0f);
+          }
+        }
+        // every drain thread's loads are done before the one arrival on the leader
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        bar_or_512(0);
+        if (threadIdx.x == 0) mbar_arrive_remote(acc_empty);
+      }
+    }
+    if (!failed) {
+      long long* part = g.partial + (int64_t)z * g.Mp * g.Np + (m0 + row) +
+                        (int64_t)(n0 + col0) * g.Mp;
+#pragma unroll
+      for (int q = 0; q < 32; ++q) part[(int64_t)q * g.Mp] = acc[q];
+    }
+    if (failed && threadIdx.x == 0) atomicExch(&s_abort, 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_abort) {
+      // this CTA's loads issued but not seen complete: wait (bounded) for them
+      for (int r = s_waited; r < s_issued; ++r)
+        mbar_wait(smem_u32(&bars[kLoaded + r % kPStages]), (uint32_t)((r / kPStages) & 1),
+                  kOzWaitLimit);
+    }
+    // the exchange: the peer arrives, then waits; the leader waits, then arrives
+    bool ok;
+    if (rank != 0) {
+      mbar_arrive_remote(cluster_addr(smem_u32(&bars[kDone]), 0));
+      ok = mbar_wait_cl(smem_u32(&bars[kDone]), 0, kOzWaitLimit);
+    } else {
+      ok = mbar_wait_cl(smem_u32(&bars[kDone]), 0, kOzWaitLimit);
+      mbar_arrive_remote(cluster_addr(smem_u32(&bars[kDone]), 1));
+    }
+    if ((s_abort || !ok) && g.status) atomicExch(g.status, (int)BTA_ERR_TIMEOUT);
+  }
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512)
                  : "memory");
   }
 }
@@ -957,14 +1351,47 @@ bta_status make_map_bf16(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap* map
 // (BTA_OZAKI_N128 = 0 / 1 forces the choice).
 struct OzPlan {
   bool n128 = false;
+  bool pair = false;   // 256 x 128 tiles on CTA pairs (implies n128)
   int splits = 1;
 };
 constexpr int kMaxSplits = 16;
 constexpr int kCtaFixedSlabs = 4;
+constexpr int kPairSlab = 13;   // a pair's slab time in sixteenths of the one-CTA kernel's
+
+// CTA pairs of the pair kernel that fit on the GPU at once (1 CTA per SM;
+// a pair needs two SMs of one cluster-capable group), queried once per device.
+int pair_slots() {
+  static int cache[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    dev = 0;
+  }
+  int* slot = dev >= 0 && dev < 64 ? &cache[dev] : nullptr;
+  if (slot && *slot > 0) return *slot;
+  int n = 0;
+  if (cudaFuncSetAttribute(ozaki_gemm_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           kPSmem) == cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * 512);
+    cfg.blockDim = dim3(kQThreads);
+    cfg.dynamicSmemBytes = kPSmem;
+    if (cudaOccupancyMaxActiveClusters(&n, ozaki_gemm_pair_kernel, &cfg) != cudaSuccess) n = 0;
+  }
+  cudaGetLastError();
+  if (n < 1) n = std::max(1, sm_count() / 2);
+  if (slot) *slot = n;
+  return n;
+}
 
 OzPlan oz_plan(int M, int N, int K, int S) {
   static const int force = [] {
     const char* v = std::getenv("BTA_OZAKI_N128");
+    return v && *v ? std::atoi(v) : -1;
+  }();
+  // BTA_OZAKI_PAIR = 1 selects the pair kernel (otherwise the one-CTA kernels)
+  static const int force_pair = [] {
+    const char* v = std::getenv("BTA_OZAKI_PAIR");
     return v && *v ? std::atoi(v) : -1;
   }();
   OzPlan p;
@@ -985,6 +1412,31 @@ OzPlan oz_plan(int M, int N, int K, int S) {
   }
   p.n128 = force == 1 || best < est64;
   if (!p.n128) p.splits = 1;
+  // Opt-in (BTA_OZAKI_PAIR = 1): measured on GB300 it is slower than the
+  // one-CTA 128 x 128 kernel (4096^3: 4.37 vs 3.78 ms; 4800^3: 7.34 vs
+  // 6.35 ms), so the plan keeps the one-CTA kernels unless asked.
+  if (force_pair != 1) return p;
+  // The pair kernel: a 256 x 128 tile per pair in about the time the one-CTA
+  // kernel spends on a 128 x 128 tile per SM, with its slabs ~kPairSlab as
+  // long (the MMAs read less shared memory).  Same wave model.
+  const int pairs = pair_slots();
+  const int64_t tp = (int64_t)cdiv(M, kPM) * cdiv(N, QN);
+  int64_t bestp = -1;
+  int sp_best = 1;
+  for (int sp = 1; sp <= kMaxSplits && sp <= nk; ++sp) {
+    if (sp > 1 && tp * sp > pairs) break;
+    const int64_t est = cdiv(tp * sp, pairs) * (cdiv(nk, sp) * kPairSlab / 16 + kCtaFixedSlabs);
+    if (bestp < 0 || est < bestp) {
+      bestp = est;
+      sp_best = sp;
+    }
+  }
+  const int64_t cur = p.n128 ? best : est64;
+  if (force_pair == 1 || bestp < cur) {
+    p.pair = true;
+    p.n128 = true;
+    p.splits = sp_best;
+  }
   return p;
 }
 
@@ -992,7 +1444,7 @@ struct OzLayout {
   int Mp, Np, Kp;
   size_t a_off, b_off, ea_off, eb_off, p_off, total;
   OzLayout(int M, int N, int K, int S, const OzPlan& plan) {
-    Mp = cdiv(M, OM) * OM;
+    Mp = plan.pair ? cdiv(M, kPM) * kPM : cdiv(M, OM) * OM;
     Np = plan.n128 ? cdiv(N, QN) * QN : cdiv(N, OBN) * OBN;
     Kp = cdiv(K, OK16) * OK16;
     auto up = [](size_t x) { return (x + 255) / 256 * 256; };
@@ -1007,8 +1459,11 @@ struct OzLayout {
   }
 };
 
+// marks (optional): two events recorded on s around the tensor-core product
+// kernel's launch alone (the measurement entry point bta_gemm_emulated_timed).
 template <int S>
-bta_status launch_ozaki(const Gemm& g, uint8_t* ws, int32_t* status, cudaStream_t s) {
+bta_status launch_ozaki(const Gemm& g, uint8_t* ws, int32_t* status, cudaStream_t s,
+                        const cudaEvent_t* marks) {
   using Cfg = OzCfg<S>;
   PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
   BTA_TRY(tensor_map_encoder(&enc));
@@ -1040,8 +1495,34 @@ bta_status launch_ozaki(const Gemm& g, uint8_t* ws, int32_t* status, cudaStream_
   const int bpitch = same ? L.Mp : L.Np;   // rows per B slice in its array
   CUtensorMap mA, mB;
   BTA_TRY(make_map_bf16(enc, &mA, YA, S * L.Mp, L.Kp, OM));
-  BTA_TRY(make_map_bf16(enc, &mB, YBm, S * bpitch, L.Kp, plan.n128 ? QN : OBN));
+  BTA_TRY(make_map_bf16(enc, &mB, YBm, S * bpitch, L.Kp,
+                        plan.pair ? kPBRows : plan.n128 ? QN : OBN));
   long long* partial = reinterpret_cast<long long*>(ws + L.p_off);
+  if (plan.pair) {
+    static bool attrp = false;
+    if (!attrp) {
+      BTA_CUDA_TRY(cudaFuncSetAttribute(ozaki_gemm_pair_kernel,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, kPSmem));
+      attrp = true;
+    }
+    OzqArgs q;
+    q.Mp = L.Mp; q.Np = L.Np; q.Bp = bpitch;
+    q.nk = L.Kp / OK16;
+    q.splits = plan.splits;
+    q.out_lower = g.out_lower;
+    q.tri_a = g.triA;
+    q.tri_b = g.triB;
+    q.partial = partial;
+    q.status = status;
+    // a wave of pairs spans a near-square patch of 256 x 128 tiles
+    q.group = std::min(L.Mp / kPM,
+                       std::max(1, (int)std::lround(std::sqrt(pair_slots() / 2.0))));
+    if (marks) BTA_CUDA_TRY(cudaEventRecord(marks[0], s));
+    ozaki_gemm_pair_kernel<<<dim3(2 * (L.Mp / kPM) * (L.Np / QN), 1, plan.splits), kQThreads,
+                             kPSmem, s>>>(mA, mB, q);
+    BTA_LAUNCHED();
+    if (marks) BTA_CUDA_TRY(cudaEventRecord(marks[1], s));
+  }
   if (plan.n128) {
     static bool attr128 = false;
     if (!attr128) {
@@ -1054,13 +1535,19 @@ bta_status launch_ozaki(const Gemm& g, uint8_t* ws, int32_t* status, cudaStream_
     q.nk = L.Kp / OK16;
     q.splits = plan.splits;
     q.out_lower = g.out_lower;
+    q.tri_a = g.triA;
+    q.tri_b = g.triB;
     q.partial = partial;
     q.status = status;
     // ~sqrt(SMs) tile rows a group: a wave of CTAs spans a near-square patch
     q.group = std::min(L.Mp / OM, std::max(1, (int)std::lround(std::sqrt((double)sm_count()))));
-    ozaki_gemm128_kernel<<<dim3((L.Mp / OM) * (L.Np / QN), 1, plan.splits), kQThreads, kQSmem,
-                           s>>>(mA, mB, q);
-    BTA_LAUNCHED();
+    if (!plan.pair) {
+      if (marks) BTA_CUDA_TRY(cudaEventRecord(marks[0], s));
+      ozaki_gemm128_kernel<<<dim3((L.Mp / OM) * (L.Np / QN), 1, plan.splits), kQThreads,
+                             kQSmem, s>>>(mA, mB, q);
+      BTA_LAUNCHED();
+      if (marks) BTA_CUDA_TRY(cudaEventRecord(marks[1], s));
+    }
     ComposeArgs c;
     c.M = M; c.N = N; c.Mp = L.Mp; c.Np = L.Np; c.splits = plan.splits;
     c.out_lower = g.out_lower;
@@ -1085,8 +1572,10 @@ bta_status launch_ozaki(const Gemm& g, uint8_t* ws, int32_t* status, cudaStream_
   a.Cin = g.Cin ? g.Cin : g.C; a.ldcin = g.Cin ? g.ldcin : g.ldc;
   a.out_lower = g.out_lower; a.exA = exA; a.exB = same ? exA : exB; a.status = status;
   a.partial = partial;
+  if (marks) BTA_CUDA_TRY(cudaEventRecord(marks[0], s));
   ozaki_gemm_kernel<S><<<dim3(L.Mp / OM, L.Np / OBN), kOzThreads, Cfg::kSmem, s>>>(mA, mB, a);
   BTA_LAUNCHED();
+  if (marks) BTA_CUDA_TRY(cudaEventRecord(marks[1], s));
   return BTA_OK;
 }
 
@@ -1103,7 +1592,12 @@ size_t ozaki_ws_bytes(int M, int N, int K, int slices) {
   const size_t part = std::max(Mq * Nq, (size_t)sm_count() * OM * QN) * 8;
   const size_t t128 = up(8 * Mq * Kp * 2) + up(8 * Nq * Kp * 2) + up(Mq * 4) + up(Nq * 4) +
                       up(part) + 256;
-  return std::max(t64, t128);
+  // pair kernel: rows padded to 256, at most one pair per two SMs per split
+  const size_t Mr = (size_t)cdiv(M, kPM) * kPM;
+  const size_t partp = std::max(Mr * Nq, (size_t)sm_count() * kPM * QN) * 8;
+  const size_t tpair = up(8 * Mr * Kp * 2) + up(8 * Nq * Kp * 2) + up(Mr * 4) + up(Nq * 4) +
+                       up(partp) + 256;
+  return std::max(t64, std::max(t128, tpair));
 }
 
 bool ozaki_supported(const Gemm& g) {
@@ -1111,15 +1605,16 @@ bool ozaki_supported(const Gemm& g) {
          g.N >= 1;
 }
 
-bta_status ozaki_gemm(const Gemm& g, void* ws, int32_t* status, int slices, cudaStream_t s) {
+bta_status ozaki_gemm(const Gemm& g, void* ws, int32_t* status, int slices, cudaStream_t s,
+                      const cudaEvent_t* marks) {
   if (g.M <= 0 || g.N <= 0) return BTA_OK;
   if (!ozaki_supported(g) || !ws) return BTA_ERR_ARG;
   uint8_t* w = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(ws) + 255) &
                                           ~(uintptr_t)255);
   switch (slices) {
-    case 6: return launch_ozaki<6>(g, w, status, s);
-    case 7: return launch_ozaki<7>(g, w, status, s);
-    case 8: return launch_ozaki<8>(g, w, status, s);
+    case 6: return launch_ozaki<6>(g, w, status, s, marks);
+    case 7: return launch_ozaki<7>(g, w, status, s, marks);
+    case 8: return launch_ozaki<8>(g, w, status, s, marks);
     default: return BTA_ERR_ARG;
   }
 }

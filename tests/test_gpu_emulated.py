@@ -139,10 +139,11 @@ def test_emulated_mode_value_backward_split(P):
     m.close()
 
 
-# ---- both GEMM kernels on every shape -------------------------------------
-# The kernel (128 x 64 tiles, or 128 x 128 tiles with split K) is chosen from
-# the shape; BTA_OZAKI_N128 = 0 / 1 forces it, read once per process, so each
-# forced run is a child process that reports max(error / bound) per shape.
+# ---- every GEMM kernel on every shape --------------------------------------
+# The kernel (128 x 64 tiles; 128 x 128 tiles with split K; 256 x 128 tiles on
+# CTA pairs with split K) is chosen from the shape; BTA_OZAKI_N128 and
+# BTA_OZAKI_PAIR force it, read once per process, so each forced run is a
+# child process that reports max(error / bound) per shape.
 _SHAPES = [(1024, 1024, 1024, False, True), (300, 200, 700, False, False),
            (130, 70, 33, True, False), (512, 256, 2048, True, True),
            (256, 256, 5120, False, True), (640, 384, 1536, True, False)]
@@ -184,10 +185,14 @@ def _child_gemm():
           flush=True)
 
 
-@pytest.mark.parametrize("force", ["0", "1"])
-def test_both_kernels_within_bound(P, force):
+@pytest.mark.parametrize("force", [
+    {"BTA_OZAKI_N128": "0", "BTA_OZAKI_PAIR": "0"},     # 128 x 64 tiles
+    {"BTA_OZAKI_N128": "1", "BTA_OZAKI_PAIR": "0"},     # 128 x 128 tiles, one CTA
+    {"BTA_OZAKI_N128": "1", "BTA_OZAKI_PAIR": "1"},     # 256 x 128 tiles, CTA pairs
+], ids=["n64", "n128", "pair"])
+def test_every_kernel_within_bound(P, force):
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    env = dict(os.environ, BTA_OZAKI_N128=force,
+    env = dict(os.environ, **force,
                PYTHONPATH=os.pathsep.join([root, os.environ.get("PYTHONPATH", "")]))
     r = subprocess.run([sys.executable, os.path.abspath(__file__)], env=env,
                        capture_output=True, text=True, timeout=900)
