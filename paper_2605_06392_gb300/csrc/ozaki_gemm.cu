@@ -53,6 +53,13 @@
 #include "common.cuh"
 #include "tma.cuh"
 
+// Timeline hooks of ozaki_gemm128_kernel (producer, MMA issuer, drain):
+// empty in the library; a measurement harness that includes this file may
+// define OZ_TRACE(event, value) before the include to record them.
+#ifndef OZ_TRACE
+#define OZ_TRACE(event, value) ((void)0)
+#endif
+
 namespace bta {
 namespace {
 
@@ -536,10 +543,92 @@ __device__ __forceinline__ void q_levels(uint32_t tmem, uint64_t dst, uint32_t f
   }
 }
 
+// The same slab in A-major order: for each 16-wide K step and A slot, its
+// pairs with B slots ascending, so consecutive MMAs read the same A tile.
+// With COLL the tensor core keeps that tile in its A collector buffer (fill on
+// the first MMA of the run, use / lastuse after) instead of re-reading shared
+// memory.  Each accumulator's first MMA in the slab is still its pair with A
+// slot 0 at K step 0.
+__host__ __device__ constexpr bool q_valid(int P, int I, int LL) {
+  return (P == 0 ? q_a0(P) + I + q_b0(P) + LL + 2 <= 5
+                 : (P == 2 ? (I + LL + 2 >= 6 && I + LL + 2 <= 8)
+                           : q_a0(P) + I + q_b0(P) + LL + 2 <= 9));
+}
+__host__ __device__ constexpr int q_lo(int P, int I) {
+  return q_valid(P, I, 0) ? 0 : q_valid(P, I, 1) ? 1 : q_valid(P, I, 2) ? 2 : q_valid(P, I, 3) ? 3 : 4;
+}
+__host__ __device__ constexpr int q_hi(int P, int I) {
+  return q_valid(P, I, 3) ? 3 : q_valid(P, I, 2) ? 2 : q_valid(P, I, 1) ? 1 : q_valid(P, I, 0) ? 0 : -1;
+}
+
+// collector op: 0 none, 1 fill, 2 use, 3 lastuse
+template <bool PAIR, int P, int I, int LL, int KK, int OP>
+__device__ __forceinline__ void q_pair_c(uint32_t tmem, uint64_t dst, uint32_t first,
+                                         uint32_t leader) {
+  if constexpr (OP == 0) {
+    q_pair<PAIR, P, I, LL, KK>(tmem, dst, first, leader);
+  } else {
+    constexpr int L = q_a0(P) + I + q_b0(P) + LL + 2;
+    constexpr int kAcc = P == 0 ? L - 2 : (L <= 7 ? L - 6 : 2);
+    constexpr bool kMayOpen = KK == 0 && I == 0 && (P == 0 || (P == 1 && L <= 8));
+    const uint32_t accumulate = kMayOpen ? (first ? 0u : 1u) : 1u;
+    constexpr unsigned long long kAo = (unsigned long long)(I * kQTile + KK * 32) >> 4;
+    constexpr unsigned long long kBo =
+        PAIR ? (unsigned long long)(4 * kQTile + LL * kPBTile + KK * 32) >> 4
+             : (unsigned long long)((4 + LL) * kQTile + KK * 32) >> 4;
+    constexpr uint32_t kId = PAIR ? kPIdesc : kQIdesc;
+#define OZ_MMA_C(GROUP, COLL)                                                                   \
+  asm volatile(                                                                                 \
+      "{\n .reg .b64 da, db;\n .reg .pred p, e;\n"                                              \
+      " add.s64 da, %1, %2;\n add.s64 db, %1, %3;\n"                                             \
+      " setp.ne.b32 p, %5, 0;\n setp.ne.b32 e, %6, 0;\n"                                         \
+      " @e tcgen05.mma.cta_group::" GROUP ".kind::f16.collector::a::" COLL " [%0], da, db, %4, p;\n}\n" \
+      ::"r"(tmem + (uint32_t)(kAcc * QN)), "l"(dst), "n"(kAo), "n"(kBo), "r"(kId),              \
+      "r"(accumulate), "r"(leader)                                                              \
+      : "memory")
+    if constexpr (PAIR) {
+      if constexpr (OP == 1) OZ_MMA_C("2", "fill");
+      else if constexpr (OP == 2) OZ_MMA_C("2", "use");
+      else OZ_MMA_C("2", "lastuse");
+    } else {
+      if constexpr (OP == 1) OZ_MMA_C("1", "fill");
+      else if constexpr (OP == 2) OZ_MMA_C("1", "use");
+      else OZ_MMA_C("1", "lastuse");
+    }
+#undef OZ_MMA_C
+  }
+}
+
+template <bool PAIR, int P, bool COLL, int KK, int I, int LL>
+__device__ __forceinline__ void q_amaj(uint32_t tmem, uint64_t dst, uint32_t first,
+                                       uint32_t leader) {
+  if constexpr (KK < 2) {
+    if constexpr (I >= 4) {
+      q_amaj<PAIR, P, COLL, KK + 1, 0, 0>(tmem, dst, first, leader);
+    } else if constexpr (LL >= 4) {
+      q_amaj<PAIR, P, COLL, KK, I + 1, 0>(tmem, dst, first, leader);
+    } else {
+      if constexpr (q_valid(P, I, LL)) {
+        constexpr int lo = q_lo(P, I), hi = q_hi(P, I);
+        constexpr int op = !COLL || lo == hi ? 0 : LL == lo ? 1 : LL == hi ? 3 : 2;
+        q_pair_c<PAIR, P, I, LL, KK, op>(tmem, dst, first, leader);
+      }
+      q_amaj<PAIR, P, COLL, KK, I, LL + 1>(tmem, dst, first, leader);
+    }
+  }
+}
+
+#ifndef OZ_SLAB_ORDER
+#define OZ_SLAB_ORDER 0
+#endif
 template <bool PAIR, int P>
 __device__ __forceinline__ void q_slab(uint32_t tmem, uint64_t dst, uint32_t first,
                                        uint32_t leader) {
-  q_levels<PAIR, P, 2>(tmem, dst, first, leader);
+  if constexpr (OZ_SLAB_ORDER == 0) {
+    q_levels<PAIR, P, 2>(tmem, dst, first, leader);
+  } else {
+    q_amaj<PAIR, P, OZ_SLAB_ORDER == 2, 0, 0, 0>(tmem, dst, first, leader);
+  }
 }
 
 // OR of v over the 512 threads of warps 0-15 (named barrier 1).
@@ -592,6 +681,45 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
   for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// 16 consecutive fp32 columns of this thread's TMEM lane, and the wait, in one
+// asm block (the registers are not read before the wait).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15}, [%16];\n tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// 8 columns at each of three TMEM addresses, one wait for all three.
+__device__ __forceinline__ void tmem_ld8x3(uint32_t a0, uint32_t a1, uint32_t a2, float (&v0)[8],
+                                           float (&v1)[8], float (&v2)[8]) {
+  uint32_t r[24];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%24];\n"
+      " tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%25];\n"
+      " tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%26];\n"
+      " tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23])
+      : "r"(a0), "r"(a1), "r"(a2)
+      : "memory");
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    v0[j] = __uint_as_float(r[j]);
+    v1[j] = __uint_as_float(r[8 + j]);
+    v2[j] = __uint_as_float(r[16 + j]);
+  }
 }
 
 // 18 warps: an SM sub-partition hosts five of them, so at most 96
@@ -649,27 +777,28 @@ __global__ void __launch_bounds__(kQThreads, 1)
 
   if (warp == 16) {
     // ---- TMA producer: for each chunk and sub-pass, the chunk's slabs of the
-    // sub-pass's slices; ring position r = running slab count
-    const uint32_t leader = lane == 0;
-    int r = 0;
-    bool stop = false;
-    for (int c = 0; c < nc && !stop; ++c) {
-      const int kt0 = ks0 + c * kChunkSlabs, kt1 = min(ks1, kt0 + kChunkSlabs);
-      for (int P = 0; P < kQPasses && !stop; ++P) {
-        const int aj0 = q_a0(P), bl0 = q_b0(P);
-        for (int kt = kt0; kt < kt1; ++kt, ++r) {
-          const int s = r % kQStages;
-          if (r >= kQStages &&
-              !warp_wait(smem_u32(&bars[kEmpty + s]), (uint32_t)((r / kQStages - 1) & 1), lane)) {
-            if (leader) atomicExch(&s_abort, 1);
-            stop = true;
-            break;
-          }
-          if (warp_flag(&s_abort, lane)) {
-            stop = true;
-            break;
-          }
-          if (leader) {
+    // sub-pass's slices; ring position r = running slab count.  Lane 0 alone
+    // runs the loop (no warp-wide step between slabs).
+    if (lane == 0) {
+      int r = 0;
+      bool stop = false;
+      for (int c = 0; c < nc && !stop; ++c) {
+        const int kt0 = ks0 + c * kChunkSlabs, kt1 = min(ks1, kt0 + kChunkSlabs);
+        for (int P = 0; P < kQPasses && !stop; ++P) {
+          const int aj0 = q_a0(P), bl0 = q_b0(P);
+          for (int kt = kt0; kt < kt1; ++kt, ++r) {
+            const int s = r % kQStages;
+            if (r >= kQStages && !mbar_wait(smem_u32(&bars[kEmpty + s]),
+                                            (uint32_t)((r / kQStages - 1) & 1), kOzWaitLimit)) {
+              atomicExch(&s_abort, 1);
+              stop = true;
+              break;
+            }
+            if (*(volatile int*)&s_abort) {
+              stop = true;
+              break;
+            }
+            OZ_TRACE(1, r);                                   // slab r's loads issued
             const uint32_t full = smem_u32(&bars[kFull + s]);
             mbar_expect_tx(full, (uint32_t)kQStage);
             uint8_t* st = smem + s * kQStage;
@@ -680,56 +809,63 @@ __global__ void __launch_bounds__(kQThreads, 1)
               tma_load_2d(smem_u32(st + (4 + l) * kQTile), &mB, full, k0, (bl0 + l) * g.Bp + n0);
             *(volatile int*)&s_issued = r + 1;
           }
-          __syncwarp();
         }
       }
     }
+    __syncwarp();
   } else if (warp == 17) {
-    // ---- MMA issuer: the whole warp runs the loop, lane 0 issues
-    const uint32_t leader = lane == 0;
-    const uint64_t dbase = sdesc64(smem_u32(smem));
-    bool stop = false;
-    int r = 0, e = 0;   // slabs consumed, accumulator sets handed to the drain
-    for (int c = 0; c < nc && !stop; ++c) {
-      const int kt0 = ks0 + c * kChunkSlabs, kt1 = min(ks1, kt0 + kChunkSlabs);
-      for (int P = 0; P < kQPasses && !stop; ++P) {
-        // P0 and P1 open an accumulator set: wait until the previous one is drained
-        if (P <= 1 && e > 0 &&
-            !warp_wait(smem_u32(&bars[kAccEmpty]), (uint32_t)((e - 1) & 1), lane)) {
-          stop = true;
-          break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        for (int kt = kt0; kt < kt1; ++kt, ++r) {
-          const int s = r % kQStages;
-          if (warp_flag(&s_abort, lane) ||
-              !warp_wait(smem_u32(&bars[kFull + s]), (uint32_t)((r / kQStages) & 1), lane)) {
+    // ---- MMA issuer: lane 0 alone runs the loop and issues every MMA, with
+    // no warp-wide step between slabs (each would leave the tensor pipe idle
+    // while the next slab's MMAs wait behind it)
+    if (lane == 0) {
+      const uint64_t dbase = sdesc64(smem_u32(smem));
+      bool stop = false;
+      int r = 0, e = 0;   // slabs consumed, accumulator sets handed to the drain
+      for (int c = 0; c < nc && !stop; ++c) {
+        const int kt0 = ks0 + c * kChunkSlabs, kt1 = min(ks1, kt0 + kChunkSlabs);
+        for (int P = 0; P < kQPasses && !stop; ++P) {
+          // P0 and P1 open an accumulator set: wait until the previous one is drained
+          OZ_TRACE(2, 4 * c + P);                            // sub-pass P wants its set
+          if (P <= 1 && e > 0 &&
+              !mbar_wait(smem_u32(&bars[kAccEmpty]), (uint32_t)((e - 1) & 1), kOzWaitLimit)) {
             stop = true;
             break;
           }
-          // (no tcgen05 fence here: the slab arrives by TMA, whose mbarrier
-          // completion already orders it before the MMAs that read it)
-          const uint64_t dst = dbase + (uint64_t)((s * kQStage) >> 4);
-          const uint32_t first = kt == kt0;
-          if (P == 0) q_slab<false, 0>(tmem, dst, first, leader);
-          else if (P == 1) q_slab<false, 1>(tmem, dst, first, leader);
-          else if (P == 2) q_slab<false, 2>(tmem, dst, first, leader);
-          else q_slab<false, 3>(tmem, dst, first, leader);
-          mma_commit_if(smem_u32(&bars[kEmpty + s]), leader);   // slab free once these finish
-          if (leader) *(volatile int*)&s_consumed = r + 1;
-          __syncwarp();
-        }
-        if (!stop && (P == 0 || P == kQPasses - 1)) {
-          mma_commit_if(smem_u32(&bars[kAccFull]), leader);   // this set's sums ready
-          ++e;
+          OZ_TRACE(3, 4 * c + P);                            // ... and starts
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          for (int kt = kt0; kt < kt1; ++kt, ++r) {
+            const int s = r % kQStages;
+            // a producer that gave up issues nothing more, so this wait runs out
+            if (!mbar_wait(smem_u32(&bars[kFull + s]), (uint32_t)((r / kQStages) & 1),
+                           kOzWaitLimit)) {
+              stop = true;
+              break;
+            }
+            OZ_TRACE(4, r);                                  // slab r in place: MMAs go
+            // (no tcgen05 fence here: the slab arrives by TMA, whose mbarrier
+            // completion already orders it before the MMAs that read it)
+            const uint64_t dst = dbase + (uint64_t)((s * kQStage) >> 4);
+            const uint32_t first = kt == kt0;
+            if (P == 0) q_slab<false, 0>(tmem, dst, first, 1u);
+            else if (P == 1) q_slab<false, 1>(tmem, dst, first, 1u);
+            else if (P == 2) q_slab<false, 2>(tmem, dst, first, 1u);
+            else q_slab<false, 3>(tmem, dst, first, 1u);
+            mma_commit_if(smem_u32(&bars[kEmpty + s]), 1u);   // slab free once these finish
+            *(volatile int*)&s_consumed = r + 1;
+          }
+          if (!stop && (P == 0 || P == kQPasses - 1)) {
+            mma_commit_if(smem_u32(&bars[kAccFull]), 1u);     // this set's sums ready
+            ++e;
+          }
         }
       }
+      if (stop) {
+        atomicExch(&s_abort, 1);
+        mma_commit_if(smem_u32(&bars[kFinal]), 1u);
+        mbar_wait(smem_u32(&bars[kFinal]), 0, kOzWaitLimit);
+      }
     }
-    if (stop) {
-      if (leader) atomicExch(&s_abort, 1);
-      mma_commit_if(smem_u32(&bars[kFinal]), leader);
-      warp_wait(smem_u32(&bars[kFinal]), 0, lane);
-    }
+    __syncwarp();
   } else {
     // ---- warps 0-15: thread = output row (TMEM lane) x 32 columns; the
     // tile's integer sums (units 2^-35 of the level-2 unit) stay in registers
@@ -746,39 +882,39 @@ __global__ void __launch_bounds__(kQThreads, 1)
           failed = 1;
           break;
         }
+        if (threadIdx.x == 0) OZ_TRACE(5, e);                // set e drain starts
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        float v[8];
         if (set == 0) {
-          // levels 2..5
+          // levels 2..5, 16 columns per TMEM round trip
 #pragma unroll
           for (int a = 0; a < 4; ++a) {
             const float up = __int_as_float((127 + 7 * a) << 23);
             const long long sc = 1ll << (7 * (5 - a));
 #pragma unroll
-            for (int hh = 0; hh < 4; ++hh) {
-              tmem_ld8(tmem + lane_off + (uint32_t)(a * QN + col0 + 8 * hh), v);
+            for (int hh = 0; hh < 2; ++hh) {
+              float v[16];
+              tmem_ld16(tmem + lane_off + (uint32_t)(a * QN + col0 + 16 * hh), v);
 #pragma unroll
-              for (int q = 0; q < 8; ++q)
-                acc[8 * hh + q] += (long long)__float2int_rn(v[q] * up) * sc;
+              for (int q = 0; q < 16; ++q)
+                acc[16 * hh + q] += (long long)__float2int_rn(v[q] * up) * sc;
             }
           }
         } else {
+          // levels 6, 7 and the rounded 8..9, 8 columns of each per round trip
 #pragma unroll
           for (int hh = 0; hh < 4; ++hh) {
-            tmem_ld8(tmem + lane_off + (uint32_t)(0 * QN + col0 + 8 * hh), v);   // level 6
+            float v6[8], v7[8], vr[8];
+            const uint32_t base = tmem + lane_off + (uint32_t)(col0 + 8 * hh);
+            tmem_ld8x3(base, base + QN, base + 2 * QN, v6, v7, vr);
 #pragma unroll
             for (int q = 0; q < 8; ++q)
-              acc[8 * hh + q] += (long long)__float2int_rn(v[q] * 268435456.0f) * 128ll;
-            tmem_ld8(tmem + lane_off + (uint32_t)(1 * QN + col0 + 8 * hh), v);   // level 7
-#pragma unroll
-            for (int q = 0; q < 8; ++q)
-              acc[8 * hh + q] += (long long)__float2int_rn(v[q] * 34359738368.0f);
-            tmem_ld8(tmem + lane_off + (uint32_t)(2 * QN + col0 + 8 * hh), v);   // levels 8, 9
-#pragma unroll
-            for (int q = 0; q < 8; ++q) acc[8 * hh + q] += __float2ll_rn(v[q] * 34359738368.0f);
+              acc[8 * hh + q] += (long long)__float2int_rn(v6[q] * 268435456.0f) * 128ll +
+                                 (long long)__float2int_rn(v7[q] * 34359738368.0f) +
+                                 __float2ll_rn(vr[q] * 34359738368.0f);
           }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        if (threadIdx.x == 0) OZ_TRACE(6, e);                // ... and ends
         mbar_arrive(smem_u32(&bars[kAccEmpty]));
       }
     }
@@ -952,27 +1088,27 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kQThreads, 1)
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 16) {
-    // ---- TMA producer (both CTAs): this CTA's halves of every slab
-    const uint32_t leader = lane == 0;
-    int r = 0;
-    bool stop = false;
-    for (int c = 0; c < nc && !stop; ++c) {
-      const int kt0 = ks0 + c * kChunkSlabs, kt1 = min(ks1, kt0 + kChunkSlabs);
-      for (int P = 0; P < kQPasses && !stop; ++P) {
-        const int aj0 = q_a0(P), bl0 = q_b0(P);
-        for (int kt = kt0; kt < kt1; ++kt, ++r) {
-          const int s = r % kPStages;
-          if (r >= kPStages && !warp_wait_cl(smem_u32(&bars[kEmpty + s]),
-                                             (uint32_t)((r / kPStages - 1) & 1), lane)) {
-            if (leader) atomicExch(&s_abort, 1);
-            stop = true;
-            break;
-          }
-          if (warp_flag(&s_abort, lane)) {
-            stop = true;
-            break;
-          }
-          if (leader) {
+    // ---- TMA producer (both CTAs): this CTA's halves of every slab; lane 0
+    // alone runs the loop
+    if (lane == 0) {
+      int r = 0;
+      bool stop = false;
+      for (int c = 0; c < nc && !stop; ++c) {
+        const int kt0 = ks0 + c * kChunkSlabs, kt1 = min(ks1, kt0 + kChunkSlabs);
+        for (int P = 0; P < kQPasses && !stop; ++P) {
+          const int aj0 = q_a0(P), bl0 = q_b0(P);
+          for (int kt = kt0; kt < kt1; ++kt, ++r) {
+            const int s = r % kPStages;
+            if (r >= kPStages && !mbar_wait_cl(smem_u32(&bars[kEmpty + s]),
+                                               (uint32_t)((r / kPStages - 1) & 1), kOzWaitLimit)) {
+              atomicExch(&s_abort, 1);
+              stop = true;
+              break;
+            }
+            if (*(volatile int*)&s_abort) {
+              stop = true;
+              break;
+            }
             const uint32_t full = smem_u32(&bars[kLoaded + s]);
             mbar_expect_tx(full, (uint32_t)kPStage);
             uint8_t* st = smem + s * kPStage;
@@ -984,83 +1120,84 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kQThreads, 1)
                           (bl0 + l) * g.Bp + nb0);
             *(volatile int*)&s_issued = r + 1;
           }
-          __syncwarp();
         }
       }
     }
+    __syncwarp();
   } else if (warp == 17 && rank != 0) {
     // ---- relay (peer CTA): each slab of this CTA in place -> the leader's `peer`
-    int r = 0;
-    bool stop = false;
-    for (int c = 0; c < nc && !stop; ++c) {
-      const int kt0 = ks0 + c * kChunkSlabs, kt1 = min(ks1, kt0 + kChunkSlabs);
-      for (int P = 0; P < kQPasses && !stop; ++P) {
-        for (int kt = kt0; kt < kt1; ++kt, ++r) {
-          const int s = r % kPStages;
-          if (warp_flag(&s_abort, lane) ||
-              !warp_wait(smem_u32(&bars[kLoaded + s]), (uint32_t)((r / kPStages) & 1), lane)) {
-            if (lane == 0) atomicExch(&s_abort, 1);
-            stop = true;
-            break;
-          }
-          if (lane == 0) {
+    if (lane == 0) {
+      int r = 0;
+      bool stop = false;
+      for (int c = 0; c < nc && !stop; ++c) {
+        const int kt0 = ks0 + c * kChunkSlabs, kt1 = min(ks1, kt0 + kChunkSlabs);
+        for (int P = 0; P < kQPasses && !stop; ++P) {
+          for (int kt = kt0; kt < kt1; ++kt, ++r) {
+            const int s = r % kPStages;
+            if (!mbar_wait(smem_u32(&bars[kLoaded + s]), (uint32_t)((r / kPStages) & 1),
+                           kOzWaitLimit)) {
+              atomicExch(&s_abort, 1);
+              stop = true;
+              break;
+            }
             mbar_arrive_remote(cluster_addr(smem_u32(&bars[kPeer + s]), 0));
             *(volatile int*)&s_waited = r + 1;
           }
-          __syncwarp();
         }
       }
     }
+    __syncwarp();
   } else if (warp == 17) {
-    // ---- MMA issuer (leader CTA): the whole warp runs the loop, lane 0 issues
-    const uint32_t leader = lane == 0;
-    const uint64_t dbase = sdesc64(smem_u32(smem));
-    bool stop = false;
-    int r = 0, e = 0;   // slabs consumed, accumulator sets handed to the drains
-    for (int c = 0; c < nc && !stop; ++c) {
-      const int kt0 = ks0 + c * kChunkSlabs, kt1 = min(ks1, kt0 + kChunkSlabs);
-      for (int P = 0; P < kQPasses && !stop; ++P) {
-        // P0 and P1 open an accumulator set: wait until both CTAs drained the last one
-        if (P <= 1 && e > 0 &&
-            !warp_wait_cl(smem_u32(&bars[kAccEmpty]), (uint32_t)((e - 1) & 1), lane)) {
-          stop = true;
-          break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        for (int kt = kt0; kt < kt1; ++kt, ++r) {
-          const int s = r % kPStages;
-          const uint32_t par = (uint32_t)((r / kPStages) & 1);
-          if (warp_flag(&s_abort, lane) || !warp_wait(smem_u32(&bars[kLoaded + s]), par, lane)) {
-            stop = true;
-            break;
-          }
-          if (leader) *(volatile int*)&s_waited = r + 1;
-          if (!warp_wait_cl(smem_u32(&bars[kPeer + s]), par, lane)) {
+    // ---- MMA issuer (leader CTA): lane 0 alone runs the loop and issues
+    if (lane == 0) {
+      const uint64_t dbase = sdesc64(smem_u32(smem));
+      bool stop = false;
+      int r = 0, e = 0;   // slabs consumed, accumulator sets handed to the drains
+      for (int c = 0; c < nc && !stop; ++c) {
+        const int kt0 = ks0 + c * kChunkSlabs, kt1 = min(ks1, kt0 + kChunkSlabs);
+        for (int P = 0; P < kQPasses && !stop; ++P) {
+          // P0 and P1 open an accumulator set: wait until both CTAs drained the last one
+          if (P <= 1 && e > 0 &&
+              !mbar_wait_cl(smem_u32(&bars[kAccEmpty]), (uint32_t)((e - 1) & 1), kOzWaitLimit)) {
             stop = true;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint64_t dst = dbase + (uint64_t)((s * kPStage) >> 4);
-          const uint32_t first = kt == kt0;
-          if (P == 0) q_slab<true, 0>(tmem, dst, first, leader);
-          else if (P == 1) q_slab<true, 1>(tmem, dst, first, leader);
-          else if (P == 2) q_slab<true, 2>(tmem, dst, first, leader);
-          else q_slab<true, 3>(tmem, dst, first, leader);
-          pair_commit_both(smem_u32(&bars[kEmpty + s]), leader);   // both halves free
-          __syncwarp();
-        }
-        if (!stop && (P == 0 || P == kQPasses - 1)) {
-          pair_commit_both(smem_u32(&bars[kAccFull]), leader);     // this set's sums ready
-          ++e;
+          for (int kt = kt0; kt < kt1; ++kt, ++r) {
+            const int s = r % kPStages;
+            const uint32_t par = (uint32_t)((r / kPStages) & 1);
+            if (!mbar_wait(smem_u32(&bars[kLoaded + s]), par, kOzWaitLimit)) {
+              stop = true;
+              break;
+            }
+            *(volatile int*)&s_waited = r + 1;
+            if (!mbar_wait_cl(smem_u32(&bars[kPeer + s]), par, kOzWaitLimit)) {
+              stop = true;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint64_t dst = dbase + (uint64_t)((s * kPStage) >> 4);
+            const uint32_t first = kt == kt0;
+            if (P == 0) q_slab<true, 0>(tmem, dst, first, 1u);
+            else if (P == 1) q_slab<true, 1>(tmem, dst, first, 1u);
+            else if (P == 2) q_slab<true, 2>(tmem, dst, first, 1u);
+            else q_slab<true, 3>(tmem, dst, first, 1u);
+            pair_commit_both(smem_u32(&bars[kEmpty + s]), 1u);   // both halves free
+          }
+          if (!stop && (P == 0 || P == kQPasses - 1)) {
+            pair_commit_both(smem_u32(&bars[kAccFull]), 1u);     // this set's sums ready
+            ++e;
+          }
         }
       }
+      if (stop) {
+        atomicExch(&s_abort, 1);
+        // wait (bounded) for the MMAs this thread issued before leaving
+        pair_commit_own(smem_u32(&bars[kFinal]), 1u);
+        mbar_wait(smem_u32(&bars[kFinal]), 0, kOzWaitLimit);
+      }
     }
-    if (stop) {
-      if (leader) atomicExch(&s_abort, 1);
-      // wait (bounded) for the MMAs this warp issued before leaving
-      pair_commit_own(smem_u32(&bars[kFinal]), leader);
-      warp_wait(smem_u32(&bars[kFinal]), 0, lane);
-    }
+    __syncwarp();
   } else if (warp < 16) {
     // ---- warps 0-15 (both CTAs): thread = output row (TMEM lane) x 32
     // columns; the tile's integer sums (units 2^-35 of the level-2 unit) stay
@@ -1080,35 +1217,33 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kQThreads, 1)
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        float v[8];
         if (set == 0) {
-          // levels 2..5
+          // levels 2..5, 16 columns per TMEM round trip
 #pragma unroll
           for (int a = 0; a < 4; ++a) {
             const float up = __int_as_float((127 + 7 * a) << 23);
             const long long sc = 1ll << (7 * (5 - a));
 #pragma unroll
-            for (int hh = 0; hh < 4; ++hh) {
-              tmem_ld8(tmem + lane_off + (uint32_t)(a * QN + col0 + 8 * hh), v);
+            for (int hh = 0; hh < 2; ++hh) {
+              float v[16];
+              tmem_ld16(tmem + lane_off + (uint32_t)(a * QN + col0 + 16 * hh), v);
 #pragma unroll
-              for (int q = 0; q < 8; ++q)
-                acc[8 * hh + q] += (long long)__float2int_rn(v[q] * up) * sc;
+              for (int q = 0; q < 16; ++q)
+                acc[16 * hh + q] += (long long)__float2int_rn(v[q] * up) * sc;
             }
           }
         } else {
+          // levels 6, 7 and the rounded 8..9, 8 columns of each per round trip
 #pragma unroll
           for (int hh = 0; hh < 4; ++hh) {
-            tmem_ld8(tmem + lane_off + (uint32_t)(0 * QN + col0 + 8 * hh), v);   // level 6
+            float v6[8], v7[8], vr[8];
+            const uint32_t base = tmem + lane_off + (uint32_t)(col0 + 8 * hh);
+            tmem_ld8x3(base, base + QN, base + 2 * QN, v6, v7, vr);
 #pragma unroll
             for (int q = 0; q < 8; ++q)
-              acc[8 * hh + q] += (long long)__float2int_rn(v[q] * 268435456.0f) * 128ll;
-            tmem_ld8(tmem + lane_off + (uint32_t)(1 * QN + col0 + 8 * hh), v);   // level 7
-#pragma unroll
-            for (int q = 0; q < 8; ++q)
-              acc[8 * hh + q] += (long long)__float2int_rn(v[q] * 34359738368.0f);
-            tmem_ld8(tmem + lane_off + (uint32_t)(2 * QN + col0 + 8 * hh), v);   // levels 8, 9
-#pragma unroll
-            for (int q = 0; q < 8; ++q) acc[8 * hh + q] += __float2ll_rn(v[q] * 34359738368.0f);
+              acc[8 * hh + q] += (long long)__float2int_rn(v6[q] * 268435456.0f) * 128ll +
+                                 (long long)__float2int_rn(v7[q] * 34359738368.0f) +
+                                 __float2ll_rn(vr[q] * 34359738368.0f);
           }
         }
         // every drain thread's loads are done before the one arrival on the leader
