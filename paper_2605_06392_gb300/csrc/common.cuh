@@ -190,9 +190,10 @@ bta_status potrf_inv_batch_prec(int count, double* const* A, int n, int ld,
 int potrf_hybrid_leaf(int precision);
 // The task-graph kernel (potrf_dag.cu) used by potrf_inv_batch for n <= 5120;
 // g_potrf_recursive = 1 selects the recursive launch sequence instead.
+// max_ctas > 0 caps the persistent grid (at least 2: the chain and a bulk CTA).
 bta_status potrf_dag_batch(int count, double* const* A, int n, int ld, double* const* scratch,
                            double* const* logdet_parts, int32_t* const* fail,
-                           const int32_t* fail_code, cudaStream_t s);
+                           const int32_t* fail_code, cudaStream_t s, int max_ctas = 0);
 extern int g_potrf_recursive;
 
 // Small helpers (sweep.cu)

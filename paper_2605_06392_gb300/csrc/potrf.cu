@@ -213,6 +213,7 @@ struct ProdCfg {
   int precision = 0;
   void* const* tcws = nullptr;
   int32_t* const* tcstat = nullptr;
+  int leaf_ctas = 0;   // cap on the task-graph grid of the leaves (0: one CTA per SM)
 };
 
 bta_status level_product(const Gemm& g, const ProdCfg& c, cudaStream_t s) {
@@ -244,7 +245,7 @@ bta_status rec_hybrid(const PB& b, int64_t aoff, int n, int ld, int64_t woff, in
       W[z] = b.W[z] + woff;
       sl[z] = b.slots[z] + soff;
     }
-    return potrf_dag_batch(cnt, A, n, ld, W, sl, b.fail, b.code, s);
+    return potrf_dag_batch(cnt, A, n, ld, W, sl, b.fail, b.code, s, pc.leaf_ctas);
   }
   const int p = n / T;
   const int n1 = (p / 2) * T, n2 = n - n1;
@@ -349,6 +350,11 @@ bta_status potrf_inv_batch_prec(int count, double* const* A, int n, int ld,
   PriorityScope prio(highest_priority());
   ProdCfg pc;
   pc.precision = precision;
+  // In the tensor-core modes the other sweep's products run on the SMs the
+  // leaves leave free: ~3/7 of the SMs keep the leaves' bulk tasks off their
+  // chain (GB300, b = 1024: mixed 126 -> 114 ms, emulated 134 -> 127 ms per
+  // gradient; the FP64 mode, whose bulk tasks need the SMs, keeps them all).
+  pc.leaf_ctas = precision ? std::max(2, sm_count() * 3 / 7) : 0;
   for (int z0 = 0; z0 < count; z0 += kMaxBatch) {
     PB b;
     b.cnt = count - z0 < kMaxBatch ? count - z0 : kMaxBatch;

@@ -593,6 +593,18 @@ int dag_ctas_per_sm() {
   return v;
 }
 
+// Most CTAs of the persistent grid (BTA_DAG_MAX_CTAS, overriding the caller's
+// cap; 0: the caller's cap, or one per SM).  A leaf's critical path is its
+// chain on one CTA; CTAs beyond what keeps its bulk tasks off that path only
+// hold SMs that a concurrent sweep's products could use.
+int dag_max_ctas() {
+  static int v = [] {
+    const char* e = getenv("BTA_DAG_MAX_CTAS");
+    return e ? atoi(e) : 0;
+  }();
+  return v;
+}
+
 // Whether bulk tasks yield the SM to chain tasks (BTA_DAG_YIELD=0 disables).
 int dag_yield() {
   static int v = [] {
@@ -628,7 +640,7 @@ size_t potrf_dag_state_ints(int p) { return (size_t)4 * p * p + p + 64 + 256; }
 // counters; n*n doubles are enough.
 bta_status potrf_dag_batch(int count, double* const* A, int n, int ld, double* const* scratch,
                            double* const* logdet_parts, int32_t* const* fail,
-                           const int32_t* fail_code, cudaStream_t s) {
+                           const int32_t* fail_code, cudaStream_t s, int max_ctas) {
   const int p = n / T;
   if (n <= 0 || n % T || p > kMaxP || count < 1) return BTA_ERR_ARG;
   const size_t lt_doubles = (size_t)p * (p - 1) / 2 * T * T;
@@ -660,7 +672,9 @@ bta_status potrf_dag_batch(int count, double* const* A, int n, int ld, double* c
     g.yield = cnt <= 2 ? dag_yield() : 0;
     g.stall = g_dag_stall;
     g.wait_ns = g_dag_wait_ns;
-    const int grid = std::min(g.total, sm_count() * dag_ctas_per_sm());
+    int grid = std::min(g.total, sm_count() * dag_ctas_per_sm());
+    const int cap = dag_max_ctas() > 0 ? dag_max_ctas() : max_ctas;
+    if (cap > 0) grid = std::min(grid, std::max(2, cap));   // the chain and a bulk CTA
     launch_prio(potrf_dag_kernel, dim3(grid), dim3(kDagThreads), s, g);
     BTA_LAUNCHED();
   }
