@@ -543,92 +543,10 @@ __device__ __forceinline__ void q_levels(uint32_t tmem, uint64_t dst, uint32_t f
   }
 }
 
-// The same slab in A-major order: for each 16-wide K step and A slot, its
-// pairs with B slots ascending, so consecutive MMAs read the same A tile.
-// With COLL the tensor core keeps that tile in its A collector buffer (fill on
-// the first MMA of the run, use / lastuse after) instead of re-reading shared
-// memory.  Each accumulator's first MMA in the slab is still its pair with A
-// slot 0 at K step 0.
-__host__ __device__ constexpr bool q_valid(int P, int I, int LL) {
-  return (P == 0 ? q_a0(P) + I + q_b0(P) + LL + 2 <= 5
-                 : (P == 2 ? (I + LL + 2 >= 6 && I + LL + 2 <= 8)
-                           : q_a0(P) + I + q_b0(P) + LL + 2 <= 9));
-}
-__host__ __device__ constexpr int q_lo(int P, int I) {
-  return q_valid(P, I, 0) ? 0 : q_valid(P, I, 1) ? 1 : q_valid(P, I, 2) ? 2 : q_valid(P, I, 3) ? 3 : 4;
-}
-__host__ __device__ constexpr int q_hi(int P, int I) {
-  return q_valid(P, I, 3) ? 3 : q_valid(P, I, 2) ? 2 : q_valid(P, I, 1) ? 1 : q_valid(P, I, 0) ? 0 : -1;
-}
-
-// collector op: 0 none, 1 fill, 2 use, 3 lastuse
-template <bool PAIR, int P, int I, int LL, int KK, int OP>
-__device__ __forceinline__ void q_pair_c(uint32_t tmem, uint64_t dst, uint32_t first,
-                                         uint32_t leader) {
-  if constexpr (OP == 0) {
-    q_pair<PAIR, P, I, LL, KK>(tmem, dst, first, leader);
-  } else {
-    constexpr int L = q_a0(P) + I + q_b0(P) + LL + 2;
-    constexpr int kAcc = P == 0 ? L - 2 : (L <= 7 ? L - 6 : 2);
-    constexpr bool kMayOpen = KK == 0 && I == 0 && (P == 0 || (P == 1 && L <= 8));
-    const uint32_t accumulate = kMayOpen ? (first ? 0u : 1u) : 1u;
-    constexpr unsigned long long kAo = (unsigned long long)(I * kQTile + KK * 32) >> 4;
-    constexpr unsigned long long kBo =
-        PAIR ? (unsigned long long)(4 * kQTile + LL * kPBTile + KK * 32) >> 4
-             : (unsigned long long)((4 + LL) * kQTile + KK * 32) >> 4;
-    constexpr uint32_t kId = PAIR ? kPIdesc : kQIdesc;
-#define OZ_MMA_C(GROUP, COLL)                                                                   \
-  asm volatile(                                                                                 \
-      "{\n .reg .b64 da, db;\n .reg .pred p, e;\n"                                              \
-      " add.s64 da, %1, %2;\n add.s64 db, %1, %3;\n"                                             \
-      " setp.ne.b32 p, %5, 0;\n setp.ne.b32 e, %6, 0;\n"                                         \
-      " @e tcgen05.mma.cta_group::" GROUP ".kind::f16.collector::a::" COLL " [%0], da, db, %4, p;\n}\n" \
-      ::"r"(tmem + (uint32_t)(kAcc * QN)), "l"(dst), "n"(kAo), "n"(kBo), "r"(kId),              \
-      "r"(accumulate), "r"(leader)                                                              \
-      : "memory")
-    if constexpr (PAIR) {
-      if constexpr (OP == 1) OZ_MMA_C("2", "fill");
-      else if constexpr (OP == 2) OZ_MMA_C("2", "use");
-      else OZ_MMA_C("2", "lastuse");
-    } else {
-      if constexpr (OP == 1) OZ_MMA_C("1", "fill");
-      else if constexpr (OP == 2) OZ_MMA_C("1", "use");
-      else OZ_MMA_C("1", "lastuse");
-    }
-#undef OZ_MMA_C
-  }
-}
-
-template <bool PAIR, int P, bool COLL, int KK, int I, int LL>
-__device__ __forceinline__ void q_amaj(uint32_t tmem, uint64_t dst, uint32_t first,
-                                       uint32_t leader) {
-  if constexpr (KK < 2) {
-    if constexpr (I >= 4) {
-      q_amaj<PAIR, P, COLL, KK + 1, 0, 0>(tmem, dst, first, leader);
-    } else if constexpr (LL >= 4) {
-      q_amaj<PAIR, P, COLL, KK, I + 1, 0>(tmem, dst, first, leader);
-    } else {
-      if constexpr (q_valid(P, I, LL)) {
-        constexpr int lo = q_lo(P, I), hi = q_hi(P, I);
-        constexpr int op = !COLL || lo == hi ? 0 : LL == lo ? 1 : LL == hi ? 3 : 2;
-        q_pair_c<PAIR, P, I, LL, KK, op>(tmem, dst, first, leader);
-      }
-      q_amaj<PAIR, P, COLL, KK, I, LL + 1>(tmem, dst, first, leader);
-    }
-  }
-}
-
-#ifndef OZ_SLAB_ORDER
-#define OZ_SLAB_ORDER 0
-#endif
 template <bool PAIR, int P>
 __device__ __forceinline__ void q_slab(uint32_t tmem, uint64_t dst, uint32_t first,
                                        uint32_t leader) {
-  if constexpr (OZ_SLAB_ORDER == 0) {
-    q_levels<PAIR, P, 2>(tmem, dst, first, leader);
-  } else {
-    q_amaj<PAIR, P, OZ_SLAB_ORDER == 2, 0, 0, 0>(tmem, dst, first, leader);
-  }
+  q_levels<PAIR, P, 2>(tmem, dst, first, leader);
 }
 
 // OR of v over the 512 threads of warps 0-15 (named barrier 1).
@@ -683,20 +601,24 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
   for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
 }
 
-// 16 consecutive fp32 columns of this thread's TMEM lane, and the wait, in one
-// asm block (the registers are not read before the wait).
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+// 8 columns at each of two TMEM addresses, one wait for both.
+__device__ __forceinline__ void tmem_ld8x2(uint32_t a0, uint32_t a1, float (&v0)[8],
+                                           float (&v1)[8]) {
   uint32_t r[16];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-      "%15}, [%16];\n tcgen05.wait::ld.sync.aligned;"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%16];\n"
+      " tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%17];\n"
+      " tcgen05.wait::ld.sync.aligned;"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
         "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
         "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr)
+      : "r"(a0), "r"(a1)
       : "memory");
 #pragma unroll
-  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+  for (int j = 0; j < 8; ++j) {
+    v0[j] = __uint_as_float(r[j]);
+    v1[j] = __uint_as_float(r[8 + j]);
+  }
 }
 
 // 8 columns at each of three TMEM addresses, one wait for all three.
@@ -885,32 +807,42 @@ __global__ void __launch_bounds__(kQThreads, 1)
         if (threadIdx.x == 0) OZ_TRACE(5, e);                // set e drain starts
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (set == 0) {
-          // levels 2..5, 16 columns per TMEM round trip
+          // levels 2..5 in pairs: over 512 of K |sum_2|, |sum_3| <= 2^23, |sum_4| <= 5 2^21,
+          // |sum_5| <= 6 2^21 (digit bounds), so x_2 128 + x_3 and x_4 128 + x_5 are exact
+          // in 32 bits; 8 columns of two levels per TMEM round trip
 #pragma unroll
-          for (int a = 0; a < 4; ++a) {
-            const float up = __int_as_float((127 + 7 * a) << 23);
-            const long long sc = 1ll << (7 * (5 - a));
+          for (int pr = 0; pr < 2; ++pr) {
+            const float up0 = __int_as_float((127 + 14 * pr) << 23);       // level 2 + 2 pr
+            const float up1 = __int_as_float((127 + 14 * pr + 7) << 23);   // level 3 + 2 pr
 #pragma unroll
-            for (int hh = 0; hh < 2; ++hh) {
-              float v[16];
-              tmem_ld16(tmem + lane_off + (uint32_t)(a * QN + col0 + 16 * hh), v);
+            for (int hh = 0; hh < 4; ++hh) {
+              float va[8], vb[8];
+              const uint32_t base = tmem + lane_off + (uint32_t)(2 * pr * QN + col0 + 8 * hh);
+              tmem_ld8x2(base, base + QN, va, vb);
 #pragma unroll
-              for (int q = 0; q < 16; ++q)
-                acc[16 * hh + q] += (long long)__float2int_rn(v[q] * up) * sc;
+              for (int q = 0; q < 8; ++q) {
+                const int c = __float2int_rn(va[q] * up0) * 128 + __float2int_rn(vb[q] * up1);
+                acc[8 * hh + q] += (long long)c << (pr == 0 ? 28 : 14);
+              }
             }
           }
         } else {
-          // levels 6, 7 and the rounded 8..9, 8 columns of each per round trip
+          // levels 6, 7 (|sum_6| <= 7 2^21, |sum_7| <= 2^24) and the rounded 8..9
+          // (|sum| 2^35 < 9.1 2^14 over 512 of K: 9 2^12 digit units per k at level 8,
+          // 10 2^12 at level 9), all three in one exact 32-bit integer; 8 columns of
+          // each per round trip
 #pragma unroll
           for (int hh = 0; hh < 4; ++hh) {
             float v6[8], v7[8], vr[8];
             const uint32_t base = tmem + lane_off + (uint32_t)(col0 + 8 * hh);
             tmem_ld8x3(base, base + QN, base + 2 * QN, v6, v7, vr);
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
-              acc[8 * hh + q] += (long long)__float2int_rn(v6[q] * 268435456.0f) * 128ll +
-                                 (long long)__float2int_rn(v7[q] * 34359738368.0f) +
-                                 __float2ll_rn(vr[q] * 34359738368.0f);
+            for (int q = 0; q < 8; ++q) {
+              const int c = __float2int_rn(v6[q] * 268435456.0f) * 128 +
+                            __float2int_rn(v7[q] * 34359738368.0f) +
+                            __float2int_rn(vr[q] * 34359738368.0f);
+              acc[8 * hh + q] += (long long)c;
+            }
           }
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -1218,32 +1150,42 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kQThreads, 1)
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (set == 0) {
-          // levels 2..5, 16 columns per TMEM round trip
+          // levels 2..5 in pairs: over 512 of K |sum_2|, |sum_3| <= 2^23, |sum_4| <= 5 2^21,
+          // |sum_5| <= 6 2^21 (digit bounds), so x_2 128 + x_3 and x_4 128 + x_5 are exact
+          // in 32 bits; 8 columns of two levels per TMEM round trip
 #pragma unroll
-          for (int a = 0; a < 4; ++a) {
-            const float up = __int_as_float((127 + 7 * a) << 23);
-            const long long sc = 1ll << (7 * (5 - a));
+          for (int pr = 0; pr < 2; ++pr) {
+            const float up0 = __int_as_float((127 + 14 * pr) << 23);       // level 2 + 2 pr
+            const float up1 = __int_as_float((127 + 14 * pr + 7) << 23);   // level 3 + 2 pr
 #pragma unroll
-            for (int hh = 0; hh < 2; ++hh) {
-              float v[16];
-              tmem_ld16(tmem + lane_off + (uint32_t)(a * QN + col0 + 16 * hh), v);
+            for (int hh = 0; hh < 4; ++hh) {
+              float va[8], vb[8];
+              const uint32_t base = tmem + lane_off + (uint32_t)(2 * pr * QN + col0 + 8 * hh);
+              tmem_ld8x2(base, base + QN, va, vb);
 #pragma unroll
-              for (int q = 0; q < 16; ++q)
-                acc[16 * hh + q] += (long long)__float2int_rn(v[q] * up) * sc;
+              for (int q = 0; q < 8; ++q) {
+                const int c = __float2int_rn(va[q] * up0) * 128 + __float2int_rn(vb[q] * up1);
+                acc[8 * hh + q] += (long long)c << (pr == 0 ? 28 : 14);
+              }
             }
           }
         } else {
-          // levels 6, 7 and the rounded 8..9, 8 columns of each per round trip
+          // levels 6, 7 (|sum_6| <= 7 2^21, |sum_7| <= 2^24) and the rounded 8..9
+          // (|sum| 2^35 < 9.1 2^14 over 512 of K: 9 2^12 digit units per k at level 8,
+          // 10 2^12 at level 9), all three in one exact 32-bit integer; 8 columns of
+          // each per round trip
 #pragma unroll
           for (int hh = 0; hh < 4; ++hh) {
             float v6[8], v7[8], vr[8];
             const uint32_t base = tmem + lane_off + (uint32_t)(col0 + 8 * hh);
             tmem_ld8x3(base, base + QN, base + 2 * QN, v6, v7, vr);
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
-              acc[8 * hh + q] += (long long)__float2int_rn(v6[q] * 268435456.0f) * 128ll +
-                                 (long long)__float2int_rn(v7[q] * 34359738368.0f) +
-                                 __float2ll_rn(vr[q] * 34359738368.0f);
+            for (int q = 0; q < 8; ++q) {
+              const int c = __float2int_rn(v6[q] * 268435456.0f) * 128 +
+                            __float2int_rn(v7[q] * 34359738368.0f) +
+                            __float2int_rn(vr[q] * 34359738368.0f);
+              acc[8 * hh + q] += (long long)c;
+            }
           }
         }
         // every drain thread's loads are done before the one arrival on the leader
@@ -1302,17 +1244,36 @@ struct ComposeArgs {
   const long long* partial;
 };
 
+// Thread: row m and kComposeCols consecutive columns, every load issued
+// before the first store (several independent loads in flight per thread).
+constexpr int kComposeCols = 4;
+
 __global__ void ozaki_compose_kernel(ComposeArgs g) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= g.M) return;
-  for (int n = blockIdx.y; n < g.N; n += gridDim.y) {
-    if (g.out_lower && m < n) break;
-    const long long* p = g.partial + m + (int64_t)n * g.Mp;
-    long long X = 0;
-    for (int z = 0; z < g.splits; ++z) X += p[(int64_t)z * g.Mp * g.Np];
-    double out = compose(X, g.exA[m] + g.exB[n] - 2093);
-    out = scale_add(out, g.amode, g.alpha, g.bmode, g.beta, g.Cin + m + (int64_t)n * g.ldcin);
-    g.C[m + (int64_t)n * g.ldc] = out;
+  const int64_t zstride = (int64_t)g.Mp * g.Np;
+  for (int n0 = blockIdx.y * kComposeCols; n0 < g.N; n0 += gridDim.y * kComposeCols) {
+    if (g.out_lower && m < n0) break;
+    long long X[kComposeCols];
+    double cin[kComposeCols];
+#pragma unroll
+    for (int c = 0; c < kComposeCols; ++c) {
+      const int n = n0 + c;
+      X[c] = 0;
+      cin[c] = 0.0;
+      if (n >= g.N || (g.out_lower && m < n)) continue;
+      const long long* p = g.partial + m + (int64_t)n * g.Mp;
+      for (int z = 0; z < g.splits; ++z) X[c] += p[(int64_t)z * zstride];
+      if (g.bmode) cin[c] = g.Cin[m + (int64_t)n * g.ldcin];
+    }
+#pragma unroll
+    for (int c = 0; c < kComposeCols; ++c) {
+      const int n = n0 + c;
+      if (n >= g.N || (g.out_lower && m < n)) continue;
+      double out = compose(X[c], g.exA[m] + g.exB[n] - 2093);
+      out = scale_add(out, g.amode, g.alpha, g.bmode, g.beta, &cin[c]);
+      g.C[m + (int64_t)n * g.ldc] = out;
+    }
   }
 }
 
@@ -1424,44 +1385,58 @@ __device__ __forceinline__ void digits(double v, int er, float (&out)[S]) {
 
 // Y[j][r][k] (j < S, r < rowsP, k < Kp; K contiguous) = digit j of
 // op(X)[r][k] times 2^(-7j); zero in the padding.  Block 256 threads over
-// 32 rows x 64 columns; each thread writes pairs of columns.
+// 32 rows x 64 columns, staged through a swizzled shared tile: column c of
+// row q sits at c ^ ((q ^ (c >> 3)) & 15), which keeps both the transposing
+// writes (16 rows, one column) and the digit reads (2 rows x 8 column groups)
+// of every half-warp on 16 distinct 8-byte banks.
+__device__ __forceinline__ int split_swz(int q, int c) { return c ^ ((q ^ (c >> 3)) & 15); }
+
 template <int S>
 __global__ void ozaki_split_kernel(SplitArgs a) {
   const SplitOp o = blockIdx.z == 0 ? a.op[0] : a.op[1];
   const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 64;
   if (r0 >= o.rowsP) return;
-  __shared__ double tile[32][65];   // tile[r - r0][k - k0]
+  __shared__ double tile[32][64];   // tile[r - r0][split_swz(r - r0, k - k0)]
   const int t = threadIdx.x;
   if (!o.trans) {
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int idx = t + 256 * i, rr = idx & 31, kk = idx >> 5;
       const int r = r0 + rr, k = k0 + kk;
-      tile[rr][kk] = (r < o.rows && k < a.K) ? op_elem(o.X, o.ldx, 0, o.tri, r, k) : 0.0;
+      tile[rr][split_swz(rr, kk)] =
+          (r < o.rows && k < a.K) ? op_elem(o.X, o.ldx, 0, o.tri, r, k) : 0.0;
     }
   } else {
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int idx = t + 256 * i, kk = idx & 63, rr = idx >> 6;
       const int r = r0 + rr, k = k0 + kk;
-      tile[rr][kk] = (r < o.rows && k < a.K) ? op_elem(o.X, o.ldx, 1, o.tri, r, k) : 0.0;
+      tile[rr][split_swz(rr, kk)] =
+          (r < o.rows && k < a.K) ? op_elem(o.X, o.ldx, 1, o.tri, r, k) : 0.0;
     }
   }
   __syncthreads();
   const size_t plane = (size_t)o.rowsP * a.Kp;
+  // thread: row q = t >> 3 and columns 8 g .. 8 g + 7, g = t & 7, so that a
+  // warp writes 4 rows x 128 contiguous bytes of each slice, one 16-byte
+  // store per thread and slice.  A digit times its power of two has at most
+  // 8 significant bits, so its BF16 pattern is the upper half of its FP32 one.
+  const int q = t >> 3, g = t & 7, r = r0 + q, k = k0 + 8 * g;
+  if (k >= a.Kp) return;   // Kp is a multiple of 32 and k of 8: k + 7 < Kp too
+  const int er = r < o.rows ? o.ex[r] : 0;
+  uint32_t w[S][4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int idx = t + 256 * i, rr = idx >> 5, kp = idx & 31;   // a warp: one row, 64 k
-    const int r = r0 + rr, k = k0 + 2 * kp;
-    if (k >= a.Kp) continue;   // Kp is a multiple of 32 and k even: k + 1 < Kp too
-    const int er = r < o.rows ? o.ex[r] : 0;
+  for (int e = 0; e < 8; e += 2) {
     float d0[S], d1[S];
-    digits<S>(tile[rr][2 * kp], er, d0);
-    digits<S>(tile[rr][2 * kp + 1], er, d1);
-    __nv_bfloat162* y = reinterpret_cast<__nv_bfloat162*>(o.Y + (size_t)r * a.Kp + k);
+    digits<S>(tile[q][split_swz(q, 8 * g + e)], er, d0);
+    digits<S>(tile[q][split_swz(q, 8 * g + e + 1)], er, d1);
 #pragma unroll
-    for (int j = 0; j < S; ++j) y[j * plane / 2] = __floats2bfloat162_rn(d0[j], d1[j]);
+    for (int j = 0; j < S; ++j)
+      w[j][e / 2] = __byte_perm(__float_as_uint(d0[j]), __float_as_uint(d1[j]), 0x7632);
   }
+  uint4* y = reinterpret_cast<uint4*>(o.Y + (size_t)r * a.Kp + k);
+#pragma unroll
+  for (int j = 0; j < S; ++j) y[j * plane / 8] = make_uint4(w[j][0], w[j][1], w[j][2], w[j][3]);
 }
 
 // 2D map over Y viewed as (S * rowsP) x Kp BF16, box 32 (K) x boxRows.
@@ -1690,7 +1665,7 @@ bta_status launch_ozaki(const Gemm& g, uint8_t* ws, int32_t* status, cudaStream_
     c.amode = alpha_mode(g.alpha); c.bmode = beta_mode(g.beta);
     c.Cin = g.Cin ? g.Cin : g.C; c.ldcin = g.Cin ? g.ldcin : g.ldc;
     c.exA = exA; c.exB = same ? exA : exB; c.partial = partial;
-    ozaki_compose_kernel<<<dim3(cdiv(M, 256), std::min(N, 65535)), 256, 0, s>>>(c);
+    ozaki_compose_kernel<<<dim3(cdiv(M, 256), std::min(cdiv(N, kComposeCols), 65535)), 256, 0, s>>>(c);
     BTA_LAUNCHED();
     return BTA_OK;
   }
