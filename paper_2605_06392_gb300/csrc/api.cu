@@ -147,8 +147,7 @@ bta_status ctx_alloc(inla_model* m, EvalCtx& c) {
   c.wsc.carve(wsbuf, ld, a);
   c.wsp.carve(wsbuf + wsb, ld, a);
   // tensor-core modes: operand copies of the tensor-core products, one per sweep
-  const size_t tcb = std::max(tc_gemm_ws_bytes(ld, ld, ld),
-                              ld <= 5120 ? ozaki_ws_bytes(ld, ld, ld, 8) : (size_t)0);
+  const size_t tcb = sweep_tc_ws_bytes(ld, a);
   uint8_t* tcbuf = nullptr;
   BTA_TRY(dmalloc(m, &tcbuf, 2 * tcb));
   c.wsc.tc = tcbuf;
@@ -537,9 +536,7 @@ bta_status bta_factor(bta_desc* q, double* rhs_inout, double* logdet, int32_t* f
   const int ld = q->ld;
   // tensor-core modes: operand copies of the b x b products (split TF32
   // planes or BF16 slices, whichever is larger), 256-byte aligned
-  const size_t tcb = precision ? std::max(tc_gemm_ws_bytes(ld, ld, ld),
-                                          ld <= 5120 ? ozaki_ws_bytes(ld, ld, ld, 8) : (size_t)0)
-                               : 0;
+  const size_t tcb = precision ? sweep_tc_ws_bytes(ld, q->a) : 0;
   const size_t head = (wsb + nsl * sizeof(double) + 255) / 256 * 256;
   uint8_t* buf = nullptr;
   BTA_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&buf), head + tcb, stream));

@@ -119,6 +119,28 @@ struct Gemm {
   double* sk_ws = nullptr;
   double* const* sk_wsb = nullptr;
   size_t sk_cap = 0;
+  // Emulated products only (ozaki_gemm, batch 1; the other GEMMs refuse a
+  // Gemm that sets any of these).  op(A) (M x K) and op(B) (K x N) as 2 x 2
+  // block matrices: op(A) = [A, A12; A21, A22] with A's block a_rows x a_k,
+  // op(B) = [B, B12; B21, B22] with B's block b_k x b_cols.  Each extra part
+  // is a plain column-major matrix (op(part) = part, or its transpose when
+  // trans is set); a null part is zero.  Only the leading blocks may be
+  // triangular (triA / triB), and only in an operand without other parts.
+  // C likewise in two row blocks: rows m < c_rows go to C / Cin (out_lower
+  // applies there), rows m >= c_rows to C2 / Cin2 (ldc2, ldcin2; full).
+  struct Part {
+    const double* X = nullptr;
+    int ld = 0, trans = 0;
+  };
+  Part A12, A21, A22, B12, B21, B22;
+  int a_rows = 0, a_k = 0, b_k = 0, b_cols = 0;   // 0: the whole of M / K / N
+  double* C2 = nullptr; int ldc2 = 0;
+  const double* Cin2 = nullptr; int ldcin2 = 0;
+  int c_rows = 0;
+  bool blocked() const {
+    return A12.X || A21.X || A22.X || B12.X || B21.X || B22.X || C2 || a_rows || a_k || b_k ||
+           b_cols || c_rows;
+  }
 };
 bta_status gemm_f64(const Gemm& g, cudaStream_t s);
 
@@ -156,7 +178,8 @@ struct TuneScope {
 bta_status tc_gemm_mixed(const Gemm& g, void* ws, int32_t* status, cudaStream_t s);
 size_t tc_gemm_ws_bytes(int M, int N, int K);
 // FP64 GEMM emulated on BF16 tensor cores with `slices` (6..8) base-128
-// digits per operand (ozaki_gemm.cu); single problem, K <= 5120.
+// digits per operand (ozaki_gemm.cu); single problem, K <= kOzakiMaxK.
+constexpr int kOzakiMaxK = 5120;   // keeps the 64-bit integer sums below 2^62.4
 // marks (optional): events recorded around the tensor-core product kernel.
 bta_status ozaki_gemm(const Gemm& g, void* ws, int32_t* status, int slices, cudaStream_t s,
                       const cudaEvent_t* marks = nullptr);

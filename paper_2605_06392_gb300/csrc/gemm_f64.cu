@@ -287,6 +287,7 @@ TuneScope::~TuneScope() { --g_tune_depth; }
 bta_status gemm_f64(const Gemm& g, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return BTA_OK;
   if (g.Ab ? !(g.Bb && g.Cb) : (g.batch != 1 || !g.A || !g.B || !g.C)) return BTA_ERR_ARG;
+  if (g.blocked()) return BTA_ERR_ARG;   // block operands: emulated products only
   const int nb = g.batch;
   const int K = g.K > 0 ? g.K : 0;
   // Tile choice.  Every tile is FP64-pipe bound and the hardware spreads

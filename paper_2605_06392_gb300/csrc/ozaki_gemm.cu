@@ -47,6 +47,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdlib>
 
@@ -71,7 +72,7 @@ constexpr int OK16 = 32;                // bf16 per K slab: 64-byte rows
 constexpr int kOzStages = 2;
 constexpr int kChunkSlabs = 16;         // exact accumulators drained every 512 of K
 constexpr int kOzThreads = 192;   // warps 0-3 drain, 4 loads, 5 issues MMAs
-constexpr int kMaxOzK = 5120;           // keeps the 64-bit integer sum below 2^62.4
+constexpr int kMaxOzK = kOzakiMaxK;
 constexpr long long kOzWaitLimit = 1ll << 21;
 constexpr int kATile = OM * OK16 * 2;   // 8 KB
 constexpr int kBTile = OBN * OK16 * 2;  // 4 KB
@@ -1239,6 +1240,12 @@ struct ComposeArgs {
   int ldc;
   const double* Cin;
   int ldcin;
+  // rows m >= c_rows (INT_MAX: none) go to C2 / Cin2, without the lower mask
+  int c_rows;
+  double* C2;
+  int ldc2;
+  const double* Cin2;
+  int ldcin2;
   const int* exA;
   const int* exB;
   const long long* partial;
@@ -1251,9 +1258,14 @@ constexpr int kComposeCols = 4;
 __global__ void ozaki_compose_kernel(ComposeArgs g) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= g.M) return;
+  const bool top = m < g.c_rows;
+  double* const Cm = top ? g.C + m : g.C2 + (m - g.c_rows);
+  const double* const Cinm = top ? g.Cin + m : g.Cin2 + (m - g.c_rows);
+  const int ldc = top ? g.ldc : g.ldc2, ldcin = top ? g.ldcin : g.ldcin2;
+  const bool lower = g.out_lower && top;
   const int64_t zstride = (int64_t)g.Mp * g.Np;
   for (int n0 = blockIdx.y * kComposeCols; n0 < g.N; n0 += gridDim.y * kComposeCols) {
-    if (g.out_lower && m < n0) break;
+    if (lower && m < n0) break;
     long long X[kComposeCols];
     double cin[kComposeCols];
 #pragma unroll
@@ -1261,18 +1273,18 @@ __global__ void ozaki_compose_kernel(ComposeArgs g) {
       const int n = n0 + c;
       X[c] = 0;
       cin[c] = 0.0;
-      if (n >= g.N || (g.out_lower && m < n)) continue;
+      if (n >= g.N || (lower && m < n)) continue;
       const long long* p = g.partial + m + (int64_t)n * g.Mp;
       for (int z = 0; z < g.splits; ++z) X[c] += p[(int64_t)z * zstride];
-      if (g.bmode) cin[c] = g.Cin[m + (int64_t)n * g.ldcin];
+      if (g.bmode) cin[c] = Cinm[(int64_t)n * ldcin];
     }
 #pragma unroll
     for (int c = 0; c < kComposeCols; ++c) {
       const int n = n0 + c;
-      if (n >= g.N || (g.out_lower && m < n)) continue;
+      if (n >= g.N || (lower && m < n)) continue;
       double out = compose(X[c], g.exA[m] + g.exB[n] - 2093);
       out = scale_add(out, g.amode, g.alpha, g.bmode, g.beta, &cin[c]);
-      g.C[m + (int64_t)n * g.ldc] = out;
+      Cm[(int64_t)n * ldc] = out;
     }
   }
 }
@@ -1287,13 +1299,42 @@ __device__ __forceinline__ double op_elem(const double* X, int ldx, int trans, i
 }
 
 // One operand to split: rows of op(X) (op(B)^T for the B side), their
-// exponent bounds ex[rowsP] and slices Y[S][rowsP][Kp].
+// exponent bounds ex[rowsP] and slices Y[S][rowsP][Kp].  op(X) may be a 2 x 2
+// block matrix cut after row rc and column kc: the leading block is (X, ldx,
+// trans, tri), the others P[0] (rows < rc, k >= kc), P[1] (rows >= rc,
+// k < kc) and P[2] (rows >= rc, k >= kc), each untriangular, zero when its
+// pointer is null.  An operand without cuts has rc = kc = INT_MAX.  The
+// leading block's trans also fixes the order in which the kernels read.
+struct SplitPart {
+  const double* X;
+  int ld, trans;
+};
 struct SplitOp {
   const double* X;
   int ldx, trans, tri, rows, rowsP;
   int* ex;
   __nv_bfloat16* Y;
+  int rc, kc;
+  SplitPart P[3];
 };
+
+// Element (r, k) of a block part (r, k within op(X) as a whole).
+__device__ __forceinline__ double op_part(const SplitOp& o, int r, int k) {
+  const bool rb = r >= o.rc, kb = k >= o.kc;
+  const SplitPart& q = !rb ? o.P[0] : !kb ? o.P[1] : o.P[2];
+  if (!q.X) return 0.0;
+  if (rb) r -= o.rc;
+  if (kb) k -= o.kc;
+  return q.trans ? q.X[k + (int64_t)r * q.ld] : q.X[r + (int64_t)k * q.ld];
+}
+
+// Element (r, k) of op(X): the leading block inline with its memory order
+// TR known at compile time, then the other parts.
+template <int TR>
+__device__ __forceinline__ double op_get(const SplitOp& o, int r, int k) {
+  if (r < o.rc && k < o.kc) return op_elem(o.X, o.ldx, TR, o.tri, r, k);
+  return op_part(o, r, k);
+}
 struct SplitArgs {
   SplitOp op[2];   // blockIdx.z selects the operand
   int K, Kp;
@@ -1317,7 +1358,7 @@ __global__ void ozaki_exp_kernel(SplitArgs a) {
     for (int i = 0; i < 8; ++i) {
       const int k = k0 + (t >> 5) + 8 * i;
       if (r < o.rows && k < a.K) {
-        const double v = op_elem(o.X, o.ldx, 0, o.tri, r, k);
+        const double v = op_get<0>(o, r, k);
         e = max(e, (int)((__double_as_longlong(v) >> 52) & 0x7FF));
       }
     }
@@ -1329,7 +1370,7 @@ __global__ void ozaki_exp_kernel(SplitArgs a) {
       const int rr = (t >> 6) + 4 * i, r = r0 + rr;
       int ei = 0;
       if (r < o.rows && k < a.K) {
-        const double v = op_elem(o.X, o.ldx, 1, o.tri, r, k);
+        const double v = op_get<1>(o, r, k);
         ei = (int)((__double_as_longlong(v) >> 52) & 0x7FF);
       }
       ei = (int)__reduce_max_sync(0xffffffffu, (unsigned)ei);   // a warp shares rr
@@ -1404,7 +1445,7 @@ __global__ void ozaki_split_kernel(SplitArgs a) {
       const int idx = t + 256 * i, rr = idx & 31, kk = idx >> 5;
       const int r = r0 + rr, k = k0 + kk;
       tile[rr][split_swz(rr, kk)] =
-          (r < o.rows && k < a.K) ? op_elem(o.X, o.ldx, 0, o.tri, r, k) : 0.0;
+          (r < o.rows && k < a.K) ? op_get<0>(o, r, k) : 0.0;
     }
   } else {
 #pragma unroll
@@ -1412,7 +1453,7 @@ __global__ void ozaki_split_kernel(SplitArgs a) {
       const int idx = t + 256 * i, kk = idx & 63, rr = idx >> 6;
       const int r = r0 + rr, k = k0 + kk;
       tile[rr][split_swz(rr, kk)] =
-          (r < o.rows && k < a.K) ? op_elem(o.X, o.ldx, 1, o.tri, r, k) : 0.0;
+          (r < o.rows && k < a.K) ? op_get<1>(o, r, k) : 0.0;
     }
   }
   __syncthreads();
@@ -1494,7 +1535,9 @@ int pair_slots() {
   return n;
 }
 
-OzPlan oz_plan(int M, int N, int K, int S) {
+// need128: the product writes a two-part C, which only the 128 x 128
+// kernel's compose pass does (S = 8).
+OzPlan oz_plan(int M, int N, int K, int S, bool need128 = false) {
   static const int force = [] {
     const char* v = std::getenv("BTA_OZAKI_N128");
     return v && *v ? std::atoi(v) : -1;
@@ -1505,7 +1548,7 @@ OzPlan oz_plan(int M, int N, int K, int S) {
     return v && *v ? std::atoi(v) : -1;
   }();
   OzPlan p;
-  if (S != 8 || force == 0) return p;
+  if (S != 8 || (force == 0 && !need128)) return p;
   const int kSmCount = sm_count();
   const int64_t nk = cdiv(K, OK16);
   const int64_t t64 = (int64_t)cdiv(M, OM) * cdiv(N, OBN);
@@ -1520,7 +1563,7 @@ OzPlan oz_plan(int M, int N, int K, int S) {
       p.splits = sp;
     }
   }
-  p.n128 = force == 1 || best < est64;
+  p.n128 = force == 1 || need128 || best < est64;
   if (!p.n128) p.splits = 1;
   // Opt-in (BTA_OZAKI_PAIR = 1): measured on GB300 it is slower than the
   // one-CTA 128 x 128 kernel (4096^3: 4.37 vs 3.78 ms; 4800^3: 7.34 vs
@@ -1578,7 +1621,8 @@ bta_status launch_ozaki(const Gemm& g, uint8_t* ws, int32_t* status, cudaStream_
   PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
   BTA_TRY(tensor_map_encoder(&enc));
   const int M = g.M, N = g.N, K = g.K;
-  const OzPlan plan = oz_plan(M, N, K, S);
+  if (g.C2 && S != 8) return BTA_ERR_ARG;
+  const OzPlan plan = oz_plan(M, N, K, S, g.C2 != nullptr);
   const OzLayout L(M, N, K, S, plan);
   __nv_bfloat16* YA = reinterpret_cast<__nv_bfloat16*>(ws + L.a_off);
   __nv_bfloat16* YB = reinterpret_cast<__nv_bfloat16*>(ws + L.b_off);
@@ -1586,14 +1630,26 @@ bta_status launch_ozaki(const Gemm& g, uint8_t* ws, int32_t* status, cudaStream_
   int* exB = reinterpret_cast<int*>(ws + L.eb_off);
   // rows of op(B)^T: Y[n][k] = op(B)[k][n]; the triangle flips with the transpose
   const int trib = g.triB == TRI_LOWER ? TRI_UPPER : g.triB == TRI_UPPER ? TRI_LOWER : TRI_NONE;
-  // op(B)^T == op(A) (the symmetric update L L^T): one set of slices serves both
+  // op(B)^T == the first N rows of op(A) (the symmetric update L L^T, with
+  // or without extra rows of A below): one set of slices serves both
+  const bool b_parts = g.B12.X || g.B21.X || g.B22.X || g.b_k || g.b_cols;
+  const bool a_kparts = g.A12.X || g.A22.X || g.a_k;
   const bool same = g.A == g.B && g.lda == g.ldb && g.transA == !g.transB && g.triA == trib &&
-                    M == N;
+                    !b_parts && !a_kparts && N <= (g.a_rows ? g.a_rows : M);
   SplitArgs sa;
   sa.K = K;
   sa.Kp = L.Kp;
-  sa.op[0] = {g.A, g.lda, g.transA, g.triA, M, L.Mp, exA, YA};
-  sa.op[1] = {g.B, g.ldb, !g.transB, trib, N, L.Np, exB, YB};
+  auto cut = [](int c) { return c > 0 ? c : INT_MAX; };
+  sa.op[0] = {g.A, g.lda, g.transA, g.triA, M, L.Mp, exA, YA, cut(g.a_rows), cut(g.a_k),
+              {{g.A12.X, g.A12.ld, g.A12.trans},
+               {g.A21.X, g.A21.ld, g.A21.trans},
+               {g.A22.X, g.A22.ld, g.A22.trans}}};
+  // the B side holds op(B)^T: its row cut is op(B)'s column cut and each
+  // part is the transpose of the matching block of op(B)
+  sa.op[1] = {g.B, g.ldb, !g.transB, trib, N, L.Np, exB, YB, cut(g.b_cols), cut(g.b_k),
+              {{g.B21.X, g.B21.ld, !g.B21.trans},
+               {g.B12.X, g.B12.ld, !g.B12.trans},
+               {g.B22.X, g.B22.ld, !g.B22.trans}}};
   const int nops = same ? 1 : 2;
   BTA_CUDA_TRY(cudaMemsetAsync(exA, 0, (size_t)L.Mp * 4, s));
   if (!same) BTA_CUDA_TRY(cudaMemsetAsync(exB, 0, (size_t)L.Np * 4, s));
@@ -1664,6 +1720,9 @@ bta_status launch_ozaki(const Gemm& g, uint8_t* ws, int32_t* status, cudaStream_
     c.alpha = g.alpha; c.beta = g.beta; c.C = g.C; c.ldc = g.ldc;
     c.amode = alpha_mode(g.alpha); c.bmode = beta_mode(g.beta);
     c.Cin = g.Cin ? g.Cin : g.C; c.ldcin = g.Cin ? g.ldcin : g.ldc;
+    c.c_rows = g.C2 ? g.c_rows : INT_MAX;
+    c.C2 = g.C2; c.ldc2 = g.ldc2;
+    c.Cin2 = g.Cin2 ? g.Cin2 : g.C2; c.ldcin2 = g.Cin2 ? g.ldcin2 : g.ldc2;
     c.exA = exA; c.exB = same ? exA : exB; c.partial = partial;
     ozaki_compose_kernel<<<dim3(cdiv(M, 256), std::min(cdiv(N, kComposeCols), 65535)), 256, 0, s>>>(c);
     BTA_LAUNCHED();
@@ -1711,8 +1770,28 @@ size_t ozaki_ws_bytes(int M, int N, int K, int slices) {
 }
 
 bool ozaki_supported(const Gemm& g) {
-  return g.batch == 1 && !g.Ab && g.A && g.B && g.C && g.K >= 1 && g.K <= kMaxOzK && g.M >= 1 &&
-         g.N >= 1;
+  if (!(g.batch == 1 && !g.Ab && g.A && g.B && g.C && g.K >= 1 && g.K <= kMaxOzK && g.M >= 1 &&
+        g.N >= 1))
+    return false;
+  if (!g.blocked()) return true;
+  // block operands: cuts inside the matrix, parts only where a cut makes
+  // room for them, no triangle in an operand with parts, C2 with its cut
+  auto in = [](int c, int n) { return c == 0 || (c > 0 && c < n); };
+  auto ok = [](const Gemm::Part& q) { return !q.X || q.ld >= 1; };
+  if (!in(g.a_rows, g.M) || !in(g.a_k, g.K) || !in(g.b_k, g.K) || !in(g.b_cols, g.N) ||
+      !in(g.c_rows, g.M))
+    return false;
+  if (!ok(g.A12) || !ok(g.A21) || !ok(g.A22) || !ok(g.B12) || !ok(g.B21) || !ok(g.B22))
+    return false;
+  if ((g.A21.X || g.A22.X) && !g.a_rows) return false;
+  if ((g.A12.X || g.A22.X) && !g.a_k) return false;
+  if ((g.B21.X || g.B22.X) && !g.b_k) return false;
+  if ((g.B12.X || g.B22.X) && !g.b_cols) return false;
+  if ((g.a_rows || g.a_k) && g.triA != TRI_NONE) return false;
+  if ((g.b_k || g.b_cols) && g.triB != TRI_NONE) return false;
+  if ((g.C2 != nullptr) != (g.c_rows > 0) || (g.C2 && g.ldc2 < 1)) return false;
+  if (g.Cin2 && g.ldcin2 < 1) return false;
+  return true;
 }
 
 bta_status ozaki_gemm(const Gemm& g, void* ws, int32_t* status, int slices, cudaStream_t s,

@@ -217,6 +217,16 @@ void SweepWs::carve(double* base, int ld, int a) {
 
 int logdet_slots(int n, int ld) { return n * potrf_inv_slots(ld) + 1; }
 
+bool arrow_fused(int ld, int a, int precision) {
+  return precision == 2 && a > 0 && ld + a <= kOzakiMaxK;
+}
+
+size_t sweep_tc_ws_bytes(int ld, int a) {
+  const int e = a > 0 && ld + a <= kOzakiMaxK ? a : 0;
+  return std::max(tc_gemm_ws_bytes(ld, ld, ld),
+                  ld <= kOzakiMaxK ? ozaki_ws_bytes(ld + e, ld, ld + e, 8) : (size_t)0);
+}
+
 
 namespace {
 
@@ -325,9 +335,43 @@ bta_status factor_sweep_multi(const SweepItem* it, int m, cudaStream_t s, cudaEv
   auto LB = [&](int z, int i) {
     return low ? ((i & 1) ? it[z].W4 : it[z].ws.W1) : B(z, i);
   };
+  // Emulated FP64: one product per matrix; the arrow rides along (arrow_fused).
+  const bool emu = precision == 2 && ld <= kOzakiMaxK;
+  auto fused = [&](int z) { return emu && arrow_fused(ld, it[z].q.a, precision); };
+  auto emulate = [&](int z, const Gemm& g) -> bta_status {
+    if (!it[z].ws.tc) return BTA_ERR_ARG;
+    return ozaki_gemm(g, it[z].ws.tc, it[z].ws.tcstat, 8, s);
+  };
+  // L_Ci (in Wc1) into C_i, then T -= L_Ci L_Ci^T
+  auto arrow_tail = [&](const std::vector<int>& grp, int i) -> bta_status {
+    const int a = it[grp[0]].q.a, c = (int)grp.size();
+    auto Ci = ptrs(grp, [&](int z) { return Cb(z, i); });
+    auto W = ptrs(grp, [&](int z) { return it[z].ws.Wc1; });
+    auto T = ptrs(grp, [&](int z) { return it[z].q.T; });
+    auto SK = ptrs(grp, [&](int z) { return it[z].ws.W3; });
+    BTA_TRY(copy_block_batch(c, cp(W), a, Ci.data(), a, a, ld, 1.0, 0, s));
+    Gemm h; h.M = a; h.N = a; h.K = ld; h.batch = c;
+    h.Ab = cp(Ci); h.lda = a; h.Bb = cp(Ci); h.ldb = a; h.transB = 1;
+    h.Cb = T.data(); h.ldc = a; h.Cinb = cp(T); h.ldcin = a; h.alpha = -1.0; h.beta = 1.0;
+    h.sk_wsb = SK.data(); h.sk_cap = blk;
+    return gemm_f64(h, s);
+  };
   for (int i = 0; i < n; ++i) {
     if (i > 0) {
-      {  // D_i -= S_{i-1} = L_B,i-1 L_B,i-1^T (lower)
+      if (emu) {  // D_i -= L_B,i-1 L_B,i-1^T (lower); rows below: C_i -= L_C,i-1 L_B,i-1^T
+        for (int z : G.all) {
+          Gemm g; g.M = ld; g.N = ld; g.K = ld;
+          g.A = LB(z, i - 1); g.lda = ld; g.B = g.A; g.ldb = ld; g.transB = 1;
+          g.C = D(z, i); g.ldc = ld; g.Cin = g.C; g.ldcin = ld;
+          g.alpha = -1.0; g.beta = 1.0; g.out_lower = 1;
+          if (fused(z)) {
+            const int a = it[z].q.a;
+            g.M = ld + a; g.a_rows = ld; g.A21 = {Cb(z, i - 1), a, 0};
+            g.c_rows = ld; g.C2 = Cb(z, i); g.ldc2 = a; g.Cin2 = g.C2; g.ldcin2 = a;
+          }
+          BTA_TRY(emulate(z, g));
+        }
+      } else {  // D_i -= S_{i-1} = L_B,i-1 L_B,i-1^T (lower)
         auto Bp = ptrs(G.all, [&](int z) { return LB(z, i - 1); });
         auto Di = ptrs(G.all, [&](int z) { return D(z, i); });
         Gemm g; g.M = ld; g.N = ld; g.K = ld; g.batch = M;
@@ -337,6 +381,7 @@ bta_status factor_sweep_multi(const SweepItem* it, int m, cudaStream_t s, cudaEv
         BTA_TRY(big_product(g, it, G.all, precision, s));
       }
       for (const auto& grp : G.arrow) {  // C_i -= L_C,i-1 L_B,i-1^T
+        if (fused(grp[0])) continue;      // carried by the product above
         const int a = it[grp[0]].q.a;
         auto Cp = ptrs(grp, [&](int z) { return Cb(z, i - 1); });
         auto Bp = ptrs(grp, [&](int z) { return LB(z, i - 1); });
@@ -366,35 +411,49 @@ bta_status factor_sweep_multi(const SweepItem* it, int m, cudaStream_t s, cudaEv
                                    code.data(), precision, tw.data(), ts.data(), s));
       if (i == 0 && mark) BTA_CUDA_TRY(cudaEventRecord(mark, s));
     }
+    const bool with_b = emu && i < n - 1;   // L_Ci as extra rows of L_Bi's product
     for (const auto& grp : G.arrow) {  // L_Ci = C_i L_Di^{-T};  T -= L_Ci L_Ci^T
+      if (with_b && fused(grp[0])) continue;
       const int a = it[grp[0]].q.a, c = (int)grp.size();
       auto Ci = ptrs(grp, [&](int z) { return Cb(z, i); });
       auto Di = ptrs(grp, [&](int z) { return D(z, i); });
       auto W = ptrs(grp, [&](int z) { return it[z].ws.Wc1; });
-      auto T = ptrs(grp, [&](int z) { return it[z].q.T; });
       auto SK = ptrs(grp, [&](int z) { return it[z].ws.W3; });
       Gemm g; g.M = a; g.N = ld; g.K = ld; g.batch = c;
       g.Ab = cp(Ci); g.lda = a; g.Bb = cp(Di); g.ldb = ld; g.transB = 1; g.triB = TRI_UPPER;
       g.Cb = W.data(); g.ldc = a;
       g.sk_wsb = SK.data(); g.sk_cap = blk;
       BTA_TRY(gemm_f64(g, s));
-      BTA_TRY(copy_block_batch(c, cp(W), a, Ci.data(), a, a, ld, 1.0, 0, s));
-      Gemm h; h.M = a; h.N = a; h.K = ld; h.batch = c;
-      h.Ab = cp(Ci); h.lda = a; h.Bb = cp(Ci); h.ldb = a; h.transB = 1;
-      h.Cb = T.data(); h.ldc = a; h.Cinb = cp(T); h.ldcin = a; h.alpha = -1.0; h.beta = 1.0;
-      h.sk_wsb = SK.data(); h.sk_cap = blk;
-      BTA_TRY(gemm_f64(h, s));
+      BTA_TRY(arrow_tail(grp, i));
     }
     if (i < n - 1) {  // L_Bi = B_i L_Di^{-T}
       if (low) BTA_TRY(assemble_b_items(it, G.all, i, s));
       auto Bi = ptrs(G.all, [&](int z) { return low ? it[z].ws.W2 : B(z, i); });
       auto Di = ptrs(G.all, [&](int z) { return D(z, i); });
       auto W = ptrs(G.all, [&](int z) { return low ? LB(z, i) : it[z].ws.W1; });
-      Gemm g; g.M = ld; g.N = ld; g.K = ld; g.batch = M;
-      g.Ab = cp(Bi); g.lda = ld; g.Bb = cp(Di); g.ldb = ld; g.transB = 1; g.triB = TRI_UPPER;
-      g.Cb = W.data(); g.ldc = ld;
-      BTA_TRY(big_product(g, it, G.all, precision, s));
+      if (emu) {  // rows below: L_Ci = C_i L_Di^{-T} into Wc1
+        for (size_t q = 0; q < G.all.size(); ++q) {
+          const int z = G.all[q];
+          Gemm g; g.M = ld; g.N = ld; g.K = ld;
+          g.A = Bi[q]; g.lda = ld; g.B = Di[q]; g.ldb = ld; g.transB = 1; g.triB = TRI_UPPER;
+          g.C = W[q]; g.ldc = ld;
+          if (fused(z)) {
+            const int a = it[z].q.a;
+            g.M = ld + a; g.a_rows = ld; g.A21 = {Cb(z, i), a, 0};
+            g.c_rows = ld; g.C2 = it[z].ws.Wc1; g.ldc2 = a;
+          }
+          BTA_TRY(emulate(z, g));
+        }
+      } else {
+        Gemm g; g.M = ld; g.N = ld; g.K = ld; g.batch = M;
+        g.Ab = cp(Bi); g.lda = ld; g.Bb = cp(Di); g.ldb = ld; g.transB = 1; g.triB = TRI_UPPER;
+        g.Cb = W.data(); g.ldc = ld;
+        BTA_TRY(big_product(g, it, G.all, precision, s));
+      }
       if (!low) BTA_TRY(copy_block_batch(M, cp(W), ld, Bi.data(), ld, ld, ld, 1.0, 0, s));
+      if (with_b)
+        for (const auto& grp : G.arrow)
+          if (fused(grp[0])) BTA_TRY(arrow_tail(grp, i));
     }
     if (!G.vec.empty()) {  // z_i = L_Di^{-1} (r_i - L_B,i-1 z_{i-1});  v_T += L_Ci z_i
       const int c = (int)G.vec.size();
@@ -627,6 +686,13 @@ bta_status selinv_sweep_multi(const SweepItem* it, int m, cudaStream_t s, int pr
   auto W2 = ptrs(G.all, [&](int z) { return it[z].ws.W2; });
   auto W3 = ptrs(G.all, [&](int z) { return it[z].ws.W3; });
   const bool low = it[0].q.B == nullptr;
+  // Emulated FP64: one product per matrix; the arrow rides along (arrow_fused).
+  const bool emu = precision == 2 && ld <= kOzakiMaxK;
+  auto fused = [&](int z) { return emu && arrow_fused(ld, it[z].q.a, precision); };
+  auto emulate = [&](int z, const Gemm& g) -> bta_status {
+    if (!it[z].ws.tc) return BTA_ERR_ARG;
+    return ozaki_gemm(g, it[z].ws.tc, it[z].ws.tcstat, 8, s);
+  };
   for (int i = n - 1; i >= 0; --i) {
     const bool hasB = i < n - 1;
     auto Di = ptrs(G.all, [&](int z) { return D(z, i); });
@@ -639,12 +705,30 @@ bta_status selinv_sweep_multi(const SweepItem* it, int m, cudaStream_t s, int pr
     }
     if (hasB) {  // W1 = F_B = L_Bi L_Di^{-1}
       auto Bi = ptrs(G.all, [&](int z) { return low ? it[z].ws.W3 : B(z, i); });
-      Gemm g; g.M = ld; g.N = ld; g.K = ld; g.batch = M;
-      g.Ab = cp(Bi); g.lda = ld; g.Bb = cp(Di); g.ldb = ld; g.triB = TRI_LOWER;
-      g.Cb = W1.data(); g.ldc = ld;
-      BTA_TRY(big_product(g, it, G.all, precision, s));
+      if (emu) {  // rows below: Wc1 = F_C = L_Ci L_Di^{-1}
+        for (size_t q = 0; q < G.all.size(); ++q) {
+          const int z = G.all[q];
+          Gemm g; g.M = ld; g.N = ld; g.K = ld;
+          g.A = Bi[q]; g.lda = ld; g.B = Di[q]; g.ldb = ld; g.triB = TRI_LOWER;
+          g.C = W1[q]; g.ldc = ld;
+          if (fused(z)) {
+            const int a = it[z].q.a;
+            g.M = ld + a; g.a_rows = ld; g.A21 = {Cb(z, i), a, 0};
+            g.c_rows = ld; g.C2 = it[z].ws.Wc1; g.ldc2 = a;
+          }
+          BTA_TRY(emulate(z, g));
+        }
+      } else {
+        Gemm g; g.M = ld; g.N = ld; g.K = ld; g.batch = M;
+        g.Ab = cp(Bi); g.lda = ld; g.Bb = cp(Di); g.ldb = ld; g.triB = TRI_LOWER;
+        g.Cb = W1.data(); g.ldc = ld;
+        BTA_TRY(big_product(g, it, G.all, precision, s));
+      }
     }
     for (const auto& grp : G.arrow) {
+      // with B_i, an arrow carried by the products (arrow_fused) gets F_C above
+      // and Z_C with Z_B below
+      if (hasB && fused(grp[0])) continue;
       const int a = it[grp[0]].q.a, c = (int)grp.size();
       auto Ci = ptrs(grp, [&](int z) { return Cb(z, i); });
       auto Dg = ptrs(grp, [&](int z) { return D(z, i); });
@@ -677,14 +761,34 @@ bta_status selinv_sweep_multi(const SweepItem* it, int m, cudaStream_t s, int pr
       }
     }
     if (hasB) {
-      {  // W2 = Z_B = -Z_D,i+1 F_B
-        auto Dn = ptrs(G.all, [&](int z) { return D(z, i + 1); });
+      auto Dn = ptrs(G.all, [&](int z) { return D(z, i + 1); });
+      if (emu) {
+        // W2 = Z_B = -Z_D,i+1 F_B; an arrow carried along as a 2 x 2 block
+        // product: [W2; Wc2] = -[Z_D,i+1, Z_C,i+1^T; Z_C,i+1, Z_T] [F_B; F_C],
+        // i.e. also W2 -= Z_C,i+1^T F_C and Wc2 = Z_C = -Z_C,i+1 F_B - Z_T F_C
+        for (size_t q = 0; q < G.all.size(); ++q) {
+          const int z = G.all[q];
+          Gemm g; g.M = ld; g.N = ld; g.K = ld;
+          g.A = Dn[q]; g.lda = ld; g.B = W1[q]; g.ldb = ld;
+          g.C = W2[q]; g.ldc = ld; g.alpha = -1.0;
+          if (fused(z)) {
+            const int a = it[z].q.a;
+            const double* Cn = Cb(z, i + 1);
+            g.M = ld + a; g.K = ld + a; g.a_rows = ld; g.a_k = ld;
+            g.A12 = {Cn, a, 1}; g.A21 = {Cn, a, 0}; g.A22 = {it[z].q.T, a, 0};
+            g.b_k = ld; g.B21 = {it[z].ws.Wc1, a, 0};
+            g.c_rows = ld; g.C2 = it[z].ws.Wc2; g.ldc2 = a;
+          }
+          BTA_TRY(emulate(z, g));
+        }
+      } else {  // W2 = Z_B = -Z_D,i+1 F_B
         Gemm g; g.M = ld; g.N = ld; g.K = ld; g.batch = M;
         g.Ab = cp(Dn); g.lda = ld; g.Bb = cp(W1); g.ldb = ld;
         g.Cb = W2.data(); g.ldc = ld; g.alpha = -1.0;
         BTA_TRY(big_product(g, it, G.all, precision, s));
       }
       for (const auto& grp : G.arrow) {  // W2 -= Z_C,i+1^T F_C
+        if (fused(grp[0])) continue;
         const int a = it[grp[0]].q.a, c = (int)grp.size();
         auto Cn = ptrs(grp, [&](int z) { return Cb(z, i + 1); });
         auto Wc1 = ptrs(grp, [&](int z) { return it[z].ws.Wc1; });
@@ -704,13 +808,30 @@ bta_status selinv_sweep_multi(const SweepItem* it, int m, cudaStream_t s, int pr
       BTA_TRY(big_product(g, it, G.all, precision, s));
     }
     if (hasB) {  // W3 -= Z_B^T F_B
-      Gemm g; g.M = ld; g.N = ld; g.K = ld; g.batch = M;
-      g.Ab = cp(W2); g.lda = ld; g.transA = 1; g.Bb = cp(W1); g.ldb = ld;
-      g.Cb = W3.data(); g.ldc = ld; g.Cinb = cp(W3); g.ldcin = ld; g.alpha = -1.0; g.beta = 1.0;
-      g.out_lower = 1;
-      BTA_TRY(big_product(g, it, G.all, precision, s));
+      if (emu) {  // an arrow carried along extends K: W3 -= [Z_B; Z_C]^T [F_B; F_C]
+        for (size_t q = 0; q < G.all.size(); ++q) {
+          const int z = G.all[q];
+          Gemm g; g.M = ld; g.N = ld; g.K = ld;
+          g.A = W2[q]; g.lda = ld; g.transA = 1; g.B = W1[q]; g.ldb = ld;
+          g.C = W3[q]; g.ldc = ld; g.Cin = W3[q]; g.ldcin = ld; g.alpha = -1.0; g.beta = 1.0;
+          g.out_lower = 1;
+          if (fused(z)) {
+            const int a = it[z].q.a;
+            g.K = ld + a; g.a_k = ld; g.A12 = {it[z].ws.Wc2, a, 1};
+            g.b_k = ld; g.B21 = {it[z].ws.Wc1, a, 0};
+          }
+          BTA_TRY(emulate(z, g));
+        }
+      } else {
+        Gemm g; g.M = ld; g.N = ld; g.K = ld; g.batch = M;
+        g.Ab = cp(W2); g.lda = ld; g.transA = 1; g.Bb = cp(W1); g.ldb = ld;
+        g.Cb = W3.data(); g.ldc = ld; g.Cinb = cp(W3); g.ldcin = ld; g.alpha = -1.0; g.beta = 1.0;
+        g.out_lower = 1;
+        BTA_TRY(big_product(g, it, G.all, precision, s));
+      }
     }
     for (const auto& grp : G.arrow) {  // W3 -= Z_C^T F_C
+      if (hasB && fused(grp[0])) continue;
       const int a = it[grp[0]].q.a, c = (int)grp.size();
       auto Wc1 = ptrs(grp, [&](int z) { return it[z].ws.Wc1; });
       auto Wc2 = ptrs(grp, [&](int z) { return it[z].ws.Wc2; });

@@ -29,6 +29,16 @@ struct SelinvFuse {
 
 int logdet_slots(int n, int ld);   // n * (ld / 32) + 1 (tip)
 
+// Emulated FP64 (precision 2) carries the arrow through the b x b products
+// of both sweeps: its a rows ride along the rows of the product that shares
+// their right-hand operand (in the row padding when b is not a multiple of
+// 128), and its rank-a terms extend K, so that no FP64 product of the a x b
+// arrow blocks with a b x b block is left per block step.
+bool arrow_fused(int ld, int a, int precision);
+// Bytes of the tensor-core workspace (SweepWs::tc) of a sweep of block size
+// ld and arrow a in any precision, the arrow-extended products included.
+size_t sweep_tc_ws_bytes(int ld, int a);
+
 // One matrix of a set swept together.  All matrices of a set share n and ld;
 // the arrow width may differ (Q_c with a > 0 next to the block-tridiagonal
 // Q_p).  Every block step of the sweep is then one launch over the set.

@@ -333,6 +333,7 @@ size_t tc_gemm_ws_bytes(int M, int N, int K) {
 bta_status tc_gemm_mixed(const Gemm& g, void* ws, int32_t* status, cudaStream_t s) {
   if (g.M <= 0 || g.N <= 0) return BTA_OK;
   if (g.batch != 1 || g.Ab || !g.A || !g.B || !g.C || g.K < 1 || !ws) return BTA_ERR_ARG;
+  if (g.blocked()) return BTA_ERR_ARG;   // block operands: emulated products only
   BTA_TRY(get_encode());
   const int M = g.M, N = g.N, K = g.K;
   const int Kp = (K + 3) / 4 * 4;
