@@ -16,6 +16,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <functional>
+#include <memory>
 #include <new>
 #include <vector>
 
@@ -176,7 +178,7 @@ bta_status ensure_ctx(inla_model* m, int count) {
   return BTA_OK;
 }
 
-// Record the evaluation of contexts 0..cnt-1.
+// The evaluation of contexts 0..cnt-1 as a list of issue steps.
 //   mode 0: f only; 1: f and gradient; 2: reverse pass of a preceding mode-0
 //   evaluation (the factors are still in place).
 // The conditional matrices Q_c of all contexts form one set and the priors
@@ -184,81 +186,121 @@ bta_status ensure_ctx(inla_model* m, int count) {
 // the two sets run on two streams.  They are independent until the final
 // combination (the stencil quadratic forms on the Q_p stream wait for x*), so
 // the serial diagonal steps of one set overlap the wide products of the other.
-bta_status record_group(inla_model* m, int mode, int cnt, int prec, cudaStream_t s0) {
+// Each step issues one block of both sweeps (Q_c's, then Q_p's), so the two
+// streams' operations, and the nodes of a captured graph, are created in
+// alternation: the driver submits a graph's kernels in creation order into a
+// bounded queue, and a whole Q_c sweep created first (~1600 launches a block)
+// held the Q_p stream back until the GPU had drained most of it.
+using IssueStep = std::function<bta_status()>;
+
+struct GroupSets {
+  std::vector<SweepItem> ic, ip;
+};
+
+bta_status group_program(inla_model* m, int mode, int cnt, int prec, cudaStream_t s0,
+                         std::vector<IssueStep>& steps) {
   const ModelDev& md = m->md;
-  const int grad = mode >= 1;
-  std::vector<SweepItem> ic(cnt), ip(cnt);
+  const int grad = mode >= 1, nt = md.nt;
+  auto sets = std::make_shared<GroupSets>();
+  sets->ic.resize(cnt);
+  sets->ip.resize(cnt);
   for (int e = 0; e < cnt; ++e) {
     EvalCtx& c = m->ctx[e];
-    ic[e].q = c.qc; ic[e].vec = c.x; ic[e].slots = c.slots_c; ic[e].fail = c.fail;
-    ic[e].ws = c.wsc; ic[e].fuse = &c.fc;
-    ip[e].q = c.qp; ip[e].vec = nullptr; ip[e].slots = c.slots_p; ip[e].fail = c.fail + 1;
-    ip[e].ws = c.wsp; ip[e].fuse = &c.fp;
-    ic[e].md = ip[e].md = &md;
-    ic[e].lay = ip[e].lay = &m->L;
-    ic[e].coef = ip[e].coef = c.coefbuf;
-    ic[e].W4 = c.w4c;
-    ip[e].W4 = c.w4p;
+    SweepItem& ic = sets->ic[e];
+    SweepItem& ip = sets->ip[e];
+    ic.q = c.qc; ic.vec = c.x; ic.slots = c.slots_c; ic.fail = c.fail;
+    ic.ws = c.wsc; ic.fuse = &c.fc;
+    ip.q = c.qp; ip.vec = nullptr; ip.slots = c.slots_p; ip.fail = c.fail + 1;
+    ip.ws = c.wsp; ip.fuse = &c.fp;
+    ic.md = ip.md = &md;
+    ic.lay = ip.lay = &m->L;
+    ic.coef = ip.coef = c.coefbuf;
+    ic.W4 = c.w4c;
+    ip.W4 = c.w4p;
   }
-  if (mode < 2) {
-    for (int e = 0; e < cnt; ++e) {
-      EvalCtx& c = m->ctx[e];
-      BTA_TRY(launch_coef(md, m->L, c.coefbuf, s0));
-      BTA_CUDA_TRY(cudaMemsetAsync(c.fail, 0xff, 2 * sizeof(int32_t), s0));
-      BTA_CUDA_TRY(cudaMemsetAsync(c.fail + 2, 0, sizeof(int32_t), s0));
-    }
-  }
-  BTA_CUDA_TRY(cudaEventRecord(m->ev0, s0));
-  // ---- stream 1: Q_c set
-  BTA_CUDA_TRY(cudaStreamWaitEvent(m->s1, m->ev0, 0));
-  if (mode < 2) {
-    for (int e = 0; e < cnt; ++e)
-      BTA_TRY(launch_assemble(md, m->L, m->ctx[e].coefbuf, 1, m->ctx[e].qc, m->ctx[e].x, m->s1));
-    BTA_TRY(factor_sweep_multi(ic.data(), cnt, m->s1, m->evd, prec));
-    BTA_TRY(upper_solve_multi(ic.data(), cnt, m->s1));
-    if (prec == 1) {
-      // one step of iterative refinement in FP64: x += Q_c^{-1} (r - Q_c x)
+  // set-up on s0, the fork, and (mode < 2) the assembly of both sets
+  steps.push_back([=]() -> bta_status {
+    if (mode < 2) {
       for (int e = 0; e < cnt; ++e) {
         EvalCtx& c = m->ctx[e];
-        BTA_TRY(launch_rhs(md, m->L, c.coefbuf, c.dr, m->s1));
-        BTA_TRY(launch_qc_residual(md, m->L, c.coefbuf, c.x, c.dr, m->s1));
-        BTA_TRY(lower_solve(c.qc, c.dr, c.wsc, m->s1));
-        BTA_TRY(upper_solve(c.qc, c.dr, c.wsc, m->s1));
-        BTA_TRY(launch_axpy((int64_t)md.nt * md.ld + md.a, 1.0, c.dr, c.x, m->s1));
+        BTA_TRY(launch_coef(md, m->L, c.coefbuf, s0));
+        BTA_CUDA_TRY(cudaMemsetAsync(c.fail, 0xff, 2 * sizeof(int32_t), s0));
+        BTA_CUDA_TRY(cudaMemsetAsync(c.fail + 2, 0, sizeof(int32_t), s0));
       }
     }
-    BTA_CUDA_TRY(cudaEventRecord(m->evx, m->s1));
-    for (int e = 0; e < cnt; ++e) BTA_TRY(launch_residual(md, m->ctx[e].x, m->ctx[e].RS, m->s1));
-  }
-  if (grad) BTA_TRY(selinv_sweep_multi(ic.data(), cnt, m->s1, prec));
-  BTA_CUDA_TRY(cudaEventRecord(m->ev1, m->s1));
-  // ---- stream 2: Q_p set
-  BTA_CUDA_TRY(cudaStreamWaitEvent(m->s2, m->ev0, 0));
+    BTA_CUDA_TRY(cudaEventRecord(m->ev0, s0));
+    BTA_CUDA_TRY(cudaStreamWaitEvent(m->s1, m->ev0, 0));
+    BTA_CUDA_TRY(cudaStreamWaitEvent(m->s2, m->ev0, 0));
+    if (mode < 2)
+      for (int e = 0; e < cnt; ++e) {
+        BTA_TRY(launch_assemble(md, m->L, m->ctx[e].coefbuf, 1, m->ctx[e].qc, m->ctx[e].x,
+                                m->s1));
+        BTA_TRY(launch_assemble(md, m->L, m->ctx[e].coefbuf, 0, m->ctx[e].qp, nullptr, m->s2));
+      }
+    return BTA_OK;
+  });
   if (mode < 2) {
-    for (int e = 0; e < cnt; ++e)
-      BTA_TRY(launch_assemble(md, m->L, m->ctx[e].coefbuf, 0, m->ctx[e].qp, nullptr, m->s2));
-    // start one diagonal step behind the Q_c sweep: the two sweeps then
-    // alternate their latency-bound diagonal factors with wide products
-    BTA_CUDA_TRY(cudaStreamWaitEvent(m->s2, m->evd, 0));
-    BTA_TRY(factor_sweep_multi(ip.data(), cnt, m->s2, nullptr, prec));
-    BTA_CUDA_TRY(cudaStreamWaitEvent(m->s2, m->evx, 0));
-    for (int e = 0; e < cnt; ++e)
-      BTA_TRY(launch_pattern_quad_all(md, m->ctx[e].x, m->ctx[e].QD, m->ctx[e].QB, m->s2));
+    for (int i = 0; i < nt; ++i)
+      steps.push_back([=]() -> bta_status {
+        BTA_TRY(factor_sweep_multi(sets->ic.data(), cnt, m->s1, m->evd, prec, i, i + 1));
+        // the Q_p sweep starts one diagonal step behind the Q_c sweep: the two
+        // then alternate their latency-bound diagonal factors with wide products
+        if (i == 0) BTA_CUDA_TRY(cudaStreamWaitEvent(m->s2, m->evd, 0));
+        return factor_sweep_multi(sets->ip.data(), cnt, m->s2, nullptr, prec, i, i + 1);
+      });
+    steps.push_back([=]() -> bta_status {
+      BTA_TRY(upper_solve_multi(sets->ic.data(), cnt, m->s1));
+      if (prec == 1) {
+        // one step of iterative refinement in FP64: x += Q_c^{-1} (r - Q_c x)
+        for (int e = 0; e < cnt; ++e) {
+          EvalCtx& c = m->ctx[e];
+          BTA_TRY(launch_rhs(md, m->L, c.coefbuf, c.dr, m->s1));
+          BTA_TRY(launch_qc_residual(md, m->L, c.coefbuf, c.x, c.dr, m->s1));
+          BTA_TRY(lower_solve(c.qc, c.dr, c.wsc, m->s1));
+          BTA_TRY(upper_solve(c.qc, c.dr, c.wsc, m->s1));
+          BTA_TRY(launch_axpy((int64_t)md.nt * md.ld + md.a, 1.0, c.dr, c.x, m->s1));
+        }
+      }
+      BTA_CUDA_TRY(cudaEventRecord(m->evx, m->s1));
+      for (int e = 0; e < cnt; ++e)
+        BTA_TRY(launch_residual(md, m->ctx[e].x, m->ctx[e].RS, m->s1));
+      BTA_CUDA_TRY(cudaStreamWaitEvent(m->s2, m->evx, 0));
+      for (int e = 0; e < cnt; ++e)
+        BTA_TRY(launch_pattern_quad_all(md, m->ctx[e].x, m->ctx[e].QD, m->ctx[e].QB, m->s2));
+      return BTA_OK;
+    });
   }
-  if (grad) BTA_TRY(selinv_sweep_multi(ip.data(), cnt, m->s2, prec));
-  BTA_CUDA_TRY(cudaEventRecord(m->ev2, m->s2));
-  // ---- join and combine
-  BTA_CUDA_TRY(cudaStreamWaitEvent(s0, m->ev1, 0));
-  BTA_CUDA_TRY(cudaStreamWaitEvent(s0, m->ev2, 0));
-  for (int e = 0; e < cnt; ++e) {
-    EvalCtx& c = m->ctx[e];
-    Reductions r{};
-    r.PDc = c.PDc; r.PBc = c.PBc; r.PCc = c.PCc; r.ZTc = c.qc.T;
-    r.PDp = c.PDp; r.PBp = c.PBp; r.QD = c.QD; r.QB = c.QB; r.RS = c.RS;
-    r.ldc = c.slots_c; r.nldc = m->nslots; r.ldp = c.slots_p; r.nldp = m->nslots;
-    r.failc = c.fail; r.failp = c.fail + 1; r.x = c.x; r.grad = grad;
-    BTA_TRY(launch_finalize(md, m->L, c.coefbuf, r, c.out, s0));
-  }
+  if (grad)
+    for (int i = nt - 1; i >= 0; --i)
+      steps.push_back([=]() -> bta_status {
+        BTA_TRY(selinv_sweep_multi(sets->ic.data(), cnt, m->s1, prec, i, i));
+        return selinv_sweep_multi(sets->ip.data(), cnt, m->s2, prec, i, i);
+      });
+  // join and combine
+  steps.push_back([=]() -> bta_status {
+    BTA_CUDA_TRY(cudaEventRecord(m->ev1, m->s1));
+    BTA_CUDA_TRY(cudaEventRecord(m->ev2, m->s2));
+    BTA_CUDA_TRY(cudaStreamWaitEvent(s0, m->ev1, 0));
+    BTA_CUDA_TRY(cudaStreamWaitEvent(s0, m->ev2, 0));
+    for (int e = 0; e < cnt; ++e) {
+      EvalCtx& c = m->ctx[e];
+      Reductions r{};
+      r.PDc = c.PDc; r.PBc = c.PBc; r.PCc = c.PCc; r.ZTc = c.qc.T;
+      r.PDp = c.PDp; r.PBp = c.PBp; r.QD = c.QD; r.QB = c.QB; r.RS = c.RS;
+      r.ldc = c.slots_c; r.nldc = m->nslots; r.ldp = c.slots_p; r.nldp = m->nslots;
+      r.failc = c.fail; r.failp = c.fail + 1; r.x = c.x; r.grad = grad;
+      BTA_TRY(launch_finalize(md, m->L, c.coefbuf, r, c.out, s0));
+    }
+    return BTA_OK;
+  });
+  return BTA_OK;
+}
+
+// Record (issue, or capture) the evaluation of contexts 0..cnt-1.
+bta_status record_group(inla_model* m, int mode, int cnt, int prec, cudaStream_t s0) {
+  std::vector<IssueStep> steps;
+  BTA_TRY(group_program(m, mode, cnt, prec, s0, steps));
+  for (auto& st : steps) BTA_TRY(st());
   return BTA_OK;
 }
 
@@ -820,14 +862,26 @@ void inla_batch_destroy(inla_batch* b) {
 }
 
 // Record every model's evaluation (theta upload, sweeps, result download)
-// as branches forked from s0.
+// as branches forked from s0.  The models' issue steps are taken round-robin
+// (step j of every model, then step j + 1), so their operations are created
+// interleaved and every model's streams start together.
 static bta_status record_batch(inla_batch* b, int grad, int prec, cudaStream_t s0) {
   BTA_CUDA_TRY(cudaEventRecord(b->fork, s0));
-  for (inla_model* m : b->models) {
+  const size_t nm = b->models.size();
+  std::vector<std::vector<IssueStep>> progs(nm);
+  size_t longest = 0;
+  for (size_t k = 0; k < nm; ++k) {
+    inla_model* m = b->models[k];
     BTA_CUDA_TRY(cudaStreamWaitEvent(m->s0, b->fork, 0));
     BTA_CUDA_TRY(cudaMemcpyAsync(m->ctx[0].coefbuf + m->L.theta, m->htheta,
                                  m->d * sizeof(double), cudaMemcpyHostToDevice, m->s0));
-    BTA_TRY(record_group(m, grad, 1, prec, m->s0));
+    BTA_TRY(group_program(m, grad, 1, prec, m->s0, progs[k]));
+    longest = std::max(longest, progs[k].size());
+  }
+  for (size_t j = 0; j < longest; ++j)
+    for (size_t k = 0; k < nm; ++k)
+      if (j < progs[k].size()) BTA_TRY(progs[k][j]());
+  for (inla_model* m : b->models) {
     BTA_CUDA_TRY(cudaMemcpyAsync(m->hout, m->ctx[0].out, out_size(m->d) * sizeof(double),
                                  cudaMemcpyDeviceToHost, m->s0));
     BTA_CUDA_TRY(cudaEventRecord(m->evj, m->s0));

@@ -10,6 +10,15 @@
 
 #include "sweep.cuh"
 
+// Phase marks of the sweeps for timeline measurements: compile-time empty in
+// the library.  A measurement build defines BTA_SWEEP_MARK(stream, tag, block)
+// to stamp the time at which the stream's work reaches that point.  Tags:
+// 0 / 3 a factor step's start / end, 1 / 2 around its diagonal factor, 4 / 5 a
+// selected-inversion step's start / end.
+#ifndef BTA_SWEEP_MARK
+#define BTA_SWEEP_MARK(s, tag, i) ((void)0)
+#endif
+
 namespace bta {
 namespace {
 
@@ -316,17 +325,20 @@ bta_status assemble_b_items(const SweepItem* it, const std::vector<int>& idx, in
 // Algorithm 1 on a set of matrices
 // ----------------------------------------------------------------------------
 bta_status factor_sweep_multi(const SweepItem* it, int m, cudaStream_t s, cudaEvent_t mark,
-                              int precision) {
+                              int precision, int i0, int i1) {
   BTA_TRY(check_set(it, m));
   const int n = it[0].q.n, ld = it[0].q.ld;
+  if (i1 < 0) i1 = n;
+  if (i0 < 0 || i0 > i1 || i1 > n) return BTA_ERR_ARG;
   const int64_t blk = (int64_t)ld * ld;
   const int p = potrf_inv_slots(ld);
   const Groups G = make_groups(it, m);
   const int M = (int)G.all.size();
-  for (int z = 0; z < m; ++z) {
-    if (it[z].q.a > 0 && it[z].vec) BTA_TRY(fill_value(it[z].ws.vT, it[z].q.a, 0.0, s));
-    BTA_TRY(fill_value(it[z].slots + (int64_t)n * p, 1, 0.0, s));
-  }
+  if (i0 == 0)
+    for (int z = 0; z < m; ++z) {
+      if (it[z].q.a > 0 && it[z].vec) BTA_TRY(fill_value(it[z].ws.vT, it[z].q.a, 0.0, s));
+      BTA_TRY(fill_value(it[z].slots + (int64_t)n * p, 1, 0.0, s));
+    }
   auto D = [&](int z, int i) { return it[z].q.D + i * blk; };
   auto B = [&](int z, int i) { return it[z].q.B + i * blk; };
   auto Cb = [&](int z, int i) { return it[z].q.C + (int64_t)i * it[z].q.a * ld; };
@@ -356,7 +368,8 @@ bta_status factor_sweep_multi(const SweepItem* it, int m, cudaStream_t s, cudaEv
     h.sk_wsb = SK.data(); h.sk_cap = blk;
     return gemm_f64(h, s);
   };
-  for (int i = 0; i < n; ++i) {
+  for (int i = i0; i < i1; ++i) {
+    BTA_SWEEP_MARK(s, 0, i);
     if (i > 0) {
       if (emu) {  // D_i -= L_B,i-1 L_B,i-1^T (lower); rows below: C_i -= L_C,i-1 L_B,i-1^T
         for (int z : G.all) {
@@ -407,8 +420,10 @@ bta_status factor_sweep_multi(const SweepItem* it, int m, cudaStream_t s, cudaEv
         tw.push_back(it[z].ws.tc);
         ts.push_back(it[z].ws.tcstat);
       }
+      BTA_SWEEP_MARK(s, 1, i);
       BTA_TRY(potrf_inv_batch_prec(M, Di.data(), ld, ld, W.data(), sl.data(), fl.data(),
                                    code.data(), precision, tw.data(), ts.data(), s));
+      BTA_SWEEP_MARK(s, 2, i);
       if (i == 0 && mark) BTA_CUDA_TRY(cudaEventRecord(mark, s));
     }
     const bool with_b = emu && i < n - 1;   // L_Ci as extra rows of L_Bi's product
@@ -477,7 +492,9 @@ bta_status factor_sweep_multi(const SweepItem* it, int m, cudaStream_t s, cudaEv
         BTA_TRY(gemv_f64(h, it[z].ws.gv, s));
       }
     }
+    BTA_SWEEP_MARK(s, 3, i);
   }
+  if (i1 < n) return BTA_OK;
   for (int z = 0; z < m; ++z) {
     const int a = it[z].q.a;
     if (a == 0) continue;
@@ -668,20 +685,24 @@ bta_status upper_solve(const bta_desc& q, double* z, const SweepWs& ws, cudaStre
 //   Z_Bi = -Z_D,i+1 F_Bi - Z_C,i+1^T F_Ci
 //   Z_Di = L_Di^{-T} L_Di^{-1} - Z_Bi^T F_Bi - Z_Ci^T F_Ci
 // ----------------------------------------------------------------------------
-bta_status selinv_sweep_multi(const SweepItem* it, int m, cudaStream_t s, int precision) {
+bta_status selinv_sweep_multi(const SweepItem* it, int m, cudaStream_t s, int precision,
+                              int i_hi, int i_lo) {
   BTA_TRY(check_set(it, m));
   const int n = it[0].q.n, ld = it[0].q.ld;
+  if (i_hi < 0) i_hi = n - 1;
+  if (i_lo < 0 || i_hi >= n || i_lo > i_hi + 1) return BTA_ERR_ARG;
   const int64_t blk = (int64_t)ld * ld;
   const Groups G = make_groups(it, m);
   const int M = (int)G.all.size();
   auto D = [&](int z, int i) { return it[z].q.D + i * blk; };
   auto B = [&](int z, int i) { return it[z].q.B + i * blk; };
   auto Cb = [&](int z, int i) { return it[z].q.C + (int64_t)i * it[z].q.a * ld; };
-  for (int z = 0; z < m; ++z) {
-    if (it[z].q.a == 0) continue;
-    tip_kernel<<<1, 32, 0, s>>>(2, it[z].q.a, it[z].q.T, nullptr, nullptr, nullptr, nullptr, 0);
-    BTA_LAUNCHED();
-  }
+  if (i_hi == n - 1)
+    for (int z = 0; z < m; ++z) {
+      if (it[z].q.a == 0) continue;
+      tip_kernel<<<1, 32, 0, s>>>(2, it[z].q.a, it[z].q.T, nullptr, nullptr, nullptr, nullptr, 0);
+      BTA_LAUNCHED();
+    }
   auto W1 = ptrs(G.all, [&](int z) { return it[z].ws.W1; });
   auto W2 = ptrs(G.all, [&](int z) { return it[z].ws.W2; });
   auto W3 = ptrs(G.all, [&](int z) { return it[z].ws.W3; });
@@ -693,7 +714,8 @@ bta_status selinv_sweep_multi(const SweepItem* it, int m, cudaStream_t s, int pr
     if (!it[z].ws.tc) return BTA_ERR_ARG;
     return ozaki_gemm(g, it[z].ws.tc, it[z].ws.tcstat, 8, s);
   };
-  for (int i = n - 1; i >= 0; --i) {
+  for (int i = i_hi; i >= i_lo; --i) {
+    BTA_SWEEP_MARK(s, 4, i);
     const bool hasB = i < n - 1;
     auto Di = ptrs(G.all, [&](int z) { return D(z, i); });
     if (hasB && low) {  // low memory: W3 = L_Bi = B_i L_Di^{-T}, B_i assembled into W2
@@ -867,6 +889,7 @@ bta_status selinv_sweep_multi(const SweepItem* it, int m, cudaStream_t s, int pr
         BTA_TRY(launch_arrow_dot(md, Cb(z, i), i, fz->PC + (int64_t)i * md.k * arrow_chunks(md),
                                  s));
     }
+    BTA_SWEEP_MARK(s, 5, i);
   }
   return BTA_OK;
 }

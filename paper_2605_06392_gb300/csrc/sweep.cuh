@@ -63,10 +63,18 @@ struct SweepItem {
 // precision 0: every product in FP64; 1: the b x b off-diagonal Schur
 // products (and the selected-inversion products) in split precision on the
 // tensor cores, the diagonal-block factorisation, arrow and log-det in FP64.
+// Block range (optional): blocks i0 <= i < i1 of the factor sweep (i1 < 0:
+// to the end) and i_hi >= i >= i_lo of the selected inversion (i_hi < 0:
+// from the last block), the set-up with the first block and the tip with
+// the last, so that consecutive ranges issue exactly the whole sweep.  A
+// caller interleaves two sweeps' ranges to create their operations (and the
+// nodes of a captured graph) in alternation.
 bta_status factor_sweep_multi(const SweepItem* items, int m, cudaStream_t s,
-                              cudaEvent_t mark = nullptr, int precision = 0);
+                              cudaEvent_t mark = nullptr, int precision = 0, int i0 = 0,
+                              int i1 = -1);
 bta_status upper_solve_multi(const SweepItem* items, int m, cudaStream_t s);
-bta_status selinv_sweep_multi(const SweepItem* items, int m, cudaStream_t s, int precision = 0);
+bta_status selinv_sweep_multi(const SweepItem* items, int m, cudaStream_t s, int precision = 0,
+                              int i_hi = -1, int i_lo = 0);
 
 bta_status factor_sweep(const bta_desc& q, double* rhs, double* slots, int32_t* fail,
                         const SweepWs& ws, cudaStream_t s, int precision = 0);
