@@ -57,14 +57,15 @@ struct PriorityScope {
 };
 int highest_priority();
 
-// Launch a kernel with the current launch priority (cudaLaunchKernelEx).
+// Launch a kernel with the current launch priority (cudaLaunchKernelEx) and
+// `smem` bytes of dynamic shared memory.
 template <class... KArgs, class... Args>
-cudaError_t launch_prio(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s,
-                        Args&&... args) {
+cudaError_t launch_prio_smem(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                             cudaStream_t s, Args&&... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = block;
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributePriority;
@@ -72,6 +73,11 @@ cudaError_t launch_prio(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStr
   cfg.attrs = attr;
   cfg.numAttrs = g_launch_priority ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+template <class... KArgs, class... Args>
+cudaError_t launch_prio(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s,
+                        Args&&... args) {
+  return launch_prio_smem(kernel, grid, block, 0, s, std::forward<Args>(args)...);
 }
 
 inline int pad_ld(int b) { return (b + kPad - 1) / kPad * kPad; }
@@ -214,9 +220,12 @@ int potrf_hybrid_leaf(int precision);
 // The task-graph kernel (potrf_dag.cu) used by potrf_inv_batch for n <= 5120;
 // g_potrf_recursive = 1 selects the recursive launch sequence instead.
 // max_ctas > 0 caps the persistent grid (at least 2: the chain and a bulk CTA).
+// tc = 1: the 32 x 32 tile products emulated in FP64 from BF16 slices on the
+// tensor cores (the tensor-core modes); 0: FP64 FMAs.
 bta_status potrf_dag_batch(int count, double* const* A, int n, int ld, double* const* scratch,
                            double* const* logdet_parts, int32_t* const* fail,
-                           const int32_t* fail_code, cudaStream_t s, int max_ctas = 0);
+                           const int32_t* fail_code, cudaStream_t s, int max_ctas = 0,
+                           int tc = 0);
 extern int g_potrf_recursive;
 
 // Small helpers (sweep.cu)

@@ -52,6 +52,7 @@
 #include <cstdlib>
 
 #include "common.cuh"
+#include "ozaki_digits.cuh"
 #include "tma.cuh"
 
 // Timeline hooks of ozaki_gemm128_kernel (producer, MMA issuer, drain):
@@ -63,6 +64,8 @@
 
 namespace bta {
 namespace {
+using oz::compose;
+using oz::digits;
 
 using namespace tc;
 
@@ -199,26 +202,6 @@ __device__ __forceinline__ double scale_add(double out, int am, double alpha, in
   if (bm == 1) out += *cin;
   else if (bm == 2) out = fma(beta, *cin, out);
   return out;
-}
-
-// X * 2^E rounded to the nearest double, from the integer X by integer
-// operations (the usual case); out-of-range exponents take ldexp.
-__device__ __forceinline__ double compose(long long X, int E) {
-  if (X == 0) return 0.0;
-  const unsigned long long sgn = X < 0 ? (1ull << 63) : 0ull;
-  unsigned long long u = X < 0 ? 0ull - (unsigned long long)X : (unsigned long long)X;
-  int lz = __clzll((long long)u);
-  u <<= lz;                                   // leading one at bit 63
-  unsigned long long m = u >> 11;             // 53 significant bits
-  const unsigned long long rem = u & 0x7FFull;
-  if (rem > 0x400ull || (rem == 0x400ull && (m & 1ull))) {
-    ++m;
-    if (m >> 53) { m >>= 1; --lz; }
-  }
-  const int be = 1023 + (63 - lz) + E;
-  if (be <= 0 || be >= 2047) return ldexp((double)X, E);
-  return __longlong_as_double((long long)(sgn | ((unsigned long long)be << 52) |
-                                          (m & ((1ull << 52) - 1))));
 }
 
 struct OzArgs {
@@ -587,19 +570,6 @@ __device__ __forceinline__ void tile_slabs(const OzqArgs& g, int m0, int rows, i
   if (ke < kb) ke = kb;
   ks0 = kb + (int)((int64_t)z * (ke - kb) / g.splits);
   ks1 = kb + (int)((int64_t)(z + 1) * (ke - kb) / g.splits);
-}
-
-// 8 consecutive fp32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
-  uint32_t r[8];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
 }
 
 // 8 columns at each of two TMEM addresses, one wait for both.
@@ -1379,49 +1349,6 @@ __global__ void ozaki_exp_kernel(SplitArgs a) {
   }
   __syncthreads();
   if (t < 32 && r0 + t < o.rows && smax[t] > 0) atomicMax(&o.ex[r0 + t], smax[t]);
-}
-
-// The S signed base-128 digits of v for the row exponent bound er, each
-// times its power of two (exact in BF16).
-template <int S>
-__device__ __forceinline__ void digits(double v, int er, float (&out)[S]) {
-  const unsigned long long bits = (unsigned long long)__double_as_longlong(v);
-  const int E = (int)((bits >> 52) & 0x7FF);
-  long long F = 0;   // v 2^(1078 - er): |F| < 2^56
-  if (E != 0) {
-    const unsigned long long mant = (bits & ((1ull << 52) - 1)) | (1ull << 52);
-    const int sh = E - er + 3;   // <= 3
-    if (sh >= 0) {
-      F = (long long)(mant << sh);
-    } else if (sh > -54) {
-      F = (long long)((mant + (1ull << (-sh - 1))) >> (-sh));
-    }
-    if (bits >> 63) F = -F;
-  }
-  // F = G 2^28 + R, R in [-2^27, 2^27): digits 1..4 from G, 5..8 from R,
-  // each taken with round-half-up so that every remainder stays within
-  // half a digit (|d_1| <= 128, |d_j| <= 64 otherwise); 32-bit arithmetic.
-  const int G0 = (int)((F + (1ll << 27)) >> 28);
-  const int R0 = (int)(F - (long long)G0 * (1ll << 28));
-  int parts[2] = {G0, R0};
-#pragma unroll
-  for (int hpart = 0; hpart < 2; ++hpart) {
-    int x = parts[hpart];
-#pragma unroll
-    for (int jj = 0; jj < 4; ++jj) {
-      const int j = 4 * hpart + jj;
-      if (j >= S) break;
-      int d;
-      if (jj < 3) {
-        const int sh = 21 - 7 * jj;
-        d = (x + (1 << (sh - 1))) >> sh;
-        x -= d * (1 << sh);
-      } else {
-        d = x;
-      }
-      out[j] = (float)d * __int_as_float((127 - 7 * j) << 23);
-    }
-  }
 }
 
 // Y[j][r][k] (j < S, r < rowsP, k < Kp; K contiguous) = digit j of

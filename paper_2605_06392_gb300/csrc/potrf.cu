@@ -245,7 +245,8 @@ bta_status rec_hybrid(const PB& b, int64_t aoff, int n, int ld, int64_t woff, in
       W[z] = b.W[z] + woff;
       sl[z] = b.slots[z] + soff;
     }
-    return potrf_dag_batch(cnt, A, n, ld, W, sl, b.fail, b.code, s, pc.leaf_ctas);
+    return potrf_dag_batch(cnt, A, n, ld, W, sl, b.fail, b.code, s, pc.leaf_ctas,
+                           pc.precision != 0);
   }
   const int p = n / T;
   const int n1 = (p / 2) * T, n2 = n - n1;

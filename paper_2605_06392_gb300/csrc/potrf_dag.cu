@@ -33,7 +33,10 @@
 #include <cstdlib>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "common.cuh"
+#include "ozaki_digits.cuh"
 
 namespace bta {
 namespace {
@@ -186,6 +189,136 @@ __device__ __forceinline__ void tile_syrk_lower(double (*L)[T + 1], double (*W)[
   }
   W[r][c] -= a00; W[r][c + 1] -= a01;
   W[r + 1][c] -= a10; W[r + 1][c + 1] -= a11;
+}
+
+// ---- emulated-FP64 tile products (tensor-core modes) -----------------------
+// out (+)= sign * X op(Y) on 32 x 32 tiles, op(Y) = Y^T (ytrans) or Y, to FP64
+// accuracy from 8 BF16 digit slices per operand on warp-level tensor-core
+// MMAs (mma.sync m16n8k16): on GB300 these run ~1900 BF16 flop per clock per
+// SM against ~1.6 FP64 FMAs, so the 36 slice-pair products of a tile cost
+// ~1.2 k clocks where its 32^3 FP64 FMAs cost ~20 k.  The digits are those
+// of the emulated GEMM (fixed point on each row's exponent bound, 7 bits a
+// digit); a level L = i + j of slice pairs sums to |S_L| < 2^21 digit units
+// over K = 32, exact in FP32; levels 0..5 are added as 64-bit integers in
+// units of 2^-35 of level 0, levels 6 and 7 rounded to that unit, and the
+// FP64 result assembled by integer operations.  Levels from 8 on are dropped,
+// the bound of the emulated GEMM with K = 32.  ylower: Y is lower triangular
+// (its upper part is not read).
+constexpr int kOzPitch = 40;                      // bf16 a slice row: 80 bytes, conflict-free ldmatrix
+constexpr int kOzPlane = T * kOzPitch;            // one 32 x 32 slice
+constexpr int kOzTileSmem = 2 * 8 * kOzPlane * 2 + 2 * T * 4;   // both operands' slices, exponents
+
+struct OzTile {
+  __nv_bfloat16* xp;   // [8][32][kOzPitch]: slices of the rows of X
+  __nv_bfloat16* yp;   // [8][32][kOzPitch]: slices of the rows of op(Y)^T
+  int* ex;             // [32] row exponents of X
+  int* ey;             // [32] row exponents of op(Y)^T
+};
+
+// Slices of a 32 x 32 matrix (element (r, k) = get(r, k)) into planes[8][r][k]
+// and its row exponent bounds e[r]: warp w takes rows w, w + 8, w + 16, w + 24.
+template <class Get>
+__device__ __forceinline__ void oz_split(Get get, __nv_bfloat16* planes, int* e) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double v[4];
+  int er[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    v[q] = get(warp + 8 * q, lane);
+    const int ef = (int)((__double_as_longlong(v[q]) >> 52) & 0x7FF);
+    er[q] = (int)__reduce_max_sync(0xffffffffu, (unsigned)ef);
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int r = warp + 8 * q;
+    float d[8];
+    oz::digits<8>(v[q], er[q], d);
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+      planes[j * kOzPlane + r * kOzPitch + lane] = __float2bfloat16_rn(d[j]);
+    if (lane == 0) e[r] = er[q];
+  }
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t (&r)[4]) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(addr)
+               : "memory");
+}
+__device__ __forceinline__ void ldsm_x2(uint32_t addr, uint32_t (&r)[2]) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];"
+               : "=r"(r[0]), "=r"(r[1])
+               : "r"(addr)
+               : "memory");
+}
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4],
+                                         const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// All 256 threads; out must not alias X or Y.  Warp w computes the 16 x 8
+// output block (rows 16 (w / 4).., columns 8 (w % 4)..).
+__device__ void tile_mm_oz(double (*X)[T + 1], double (*Y)[T + 1], bool ytrans, bool ylower,
+                           double (*out)[T + 1], double sign, bool accumulate,
+                           const OzTile& z) {
+  const bool same = X == Y && ytrans && !ylower;   // X op(Y) = X X^T: one split
+  oz_split([&](int r, int k) { return X[r][k]; }, z.xp, z.ex);
+  if (!same)
+    oz_split(
+        [&](int n, int k) {
+          const double v = ytrans ? Y[n][k] : Y[k][n];
+          return ylower && (ytrans ? k > n : n > k) ? 0.0 : v;
+        },
+        z.yp, z.ey);
+  __syncthreads();
+  const __nv_bfloat16* yp = same ? z.xp : z.yp;
+  const int* ey = same ? z.ex : z.ey;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int mt = warp >> 2, nt = warp & 3;
+  uint32_t a[8][2][4], b[8][2][2];
+  {
+    const uint32_t xb = (uint32_t)__cvta_generic_to_shared(z.xp);
+    const uint32_t yb = (uint32_t)__cvta_generic_to_shared(yp);
+    // ldmatrix rows: A's four 8 x 8 blocks (rows 0-7 / 8-15 by k 0-7 / 8-15),
+    // B's two (columns 0-7 by k 0-7 / 8-15), from lanes 0-31 / 0-15
+    const int ar = 16 * mt + (lane & 7) + ((lane >> 3) & 1) * 8, ac = (lane >> 4) * 8;
+    const int br = 8 * nt + (lane & 7), bc = ((lane >> 3) & 1) * 8;
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks) {
+        ldsm_x4(xb + 2u * (uint32_t)(j * kOzPlane + ar * kOzPitch + 16 * ks + ac), a[j][ks]);
+        ldsm_x2(yb + 2u * (uint32_t)(j * kOzPlane + br * kOzPitch + 16 * ks + bc), b[j][ks]);
+      }
+  }
+  long long tot[4] = {0, 0, 0, 0};
+  float low[4] = {0.f, 0.f, 0.f, 0.f};   // levels 6 and 7
+#pragma unroll
+  for (int L = 0; L < 8; ++L) {
+    float c[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int i = 0; i <= L; ++i)
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks) mma_bf16(c, a[i][ks], b[L - i][ks]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (L < 6) tot[q] += __float2ll_rn(c[q] * 34359738368.0f);   // S_L 2^(35 - 7 L)
+      else low[q] += c[q];
+    }
+  }
+  const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    tot[q] += __float2ll_rn(low[q] * 34359738368.0f);
+    const int r = 16 * mt + g + (q >> 1) * 8, c = 8 * nt + 2 * t + (q & 1);
+    const double v = oz::compose(tot[q], z.ex[r] + ey[c] - 2093);
+    out[r][c] = accumulate ? fma(sign, v, out[r][c]) : sign * v;
+  }
 }
 
 struct Task {
@@ -387,10 +520,29 @@ __device__ __forceinline__ void leaf_logdet(const double* piv, double* slot, int
   }
 }
 
+// TC: the tile products emulated in FP64 on the tensor cores (tile_mm_oz,
+// the tensor-core modes); otherwise FP64 FMAs.
+template <bool TC>
 __global__ void __launch_bounds__(kDagThreads) potrf_dag_kernel(DagArgs g) {
-  // three tiles (~26 KB with the leaf's vectors): a CTA fits beside a
-  // tensor-core GEMM CTA of the other sweep on the same SM
+  // three tiles (~26 KB with the leaf's vectors); TC adds the slices of two
+  // tiles (40 KB of dynamic shared memory)
   __shared__ double S0[T][T + 1], S1[T][T + 1], S2[T][T + 1];
+  extern __shared__ __align__(16) unsigned char dsm[];
+  OzTile ozs;
+  ozs.xp = reinterpret_cast<__nv_bfloat16*>(dsm);
+  ozs.yp = ozs.xp + 8 * kOzPlane;
+  ozs.ex = reinterpret_cast<int*>(ozs.yp + 8 * kOzPlane);
+  ozs.ey = ozs.ex + T;
+  // out (+)= sign X op(Y), and the product with a lower-triangular Y^T
+  auto mm = [&](double (*X)[T + 1], double (*Y)[T + 1], bool ytrans, double (*o)[T + 1],
+                double sign, bool acc) {
+    if constexpr (TC) tile_mm_oz(X, Y, ytrans, false, o, sign, acc, ozs);
+    else tile_mm(X, Y, ytrans, o, sign, acc);
+  };
+  auto mm_lt = [&](double (*W)[T + 1], double (*Y)[T + 1], double (*o)[T + 1]) {
+    if constexpr (TC) tile_mm_oz(W, Y, true, true, o, 1.0, false, ozs);
+    else tile_mm_lt(W, Y, o);
+  };
   __shared__ double lcol[2][T], piv[T], rs[T];
   __shared__ int s_task, s_ok;
   const int p = g.p, ld = g.ld, pp = p * p;
@@ -458,7 +610,7 @@ __global__ void __launch_bounds__(kDagThreads) potrf_dag_kernel(DagArgs g) {
             }
           }
           __syncthreads();
-          tile_mm_lt(S0, S1, S2);                 // L_{c,c-1} = W X_{c-1,c-1}^T (S1)
+          mm_lt(S0, S1, S2);                      // L_{c,c-1} = W X_{c-1,c-1}^T (S1)
           __syncthreads();
 #pragma unroll
           for (int q = 0; q < T * T / kDagThreads; ++q) {
@@ -468,7 +620,8 @@ __global__ void __launch_bounds__(kDagThreads) potrf_dag_kernel(DagArgs g) {
           store_tile(Lt(c, c - 1), T, S2, false);
           __syncthreads();
           if (threadIdx.x == 0) { __threadfence(); st_release(&doneS[c * p + c - 1], 1); }
-          tile_syrk_lower(S2, S0);                // W_cc -= L L^T (lower)
+          if constexpr (TC) tile_mm_oz(S2, S2, true, false, S0, -1.0, true, ozs);   // W_cc -= L L^T
+          else tile_syrk_lower(S2, S0);           // W_cc -= L L^T (lower)
           __syncthreads();
         } else {
           load_tile(S0, tile(I.A, ld, 0, 0), ld);
@@ -522,7 +675,7 @@ __global__ void __launch_bounds__(kDagThreads) potrf_dag_kernel(DagArgs g) {
         load_tile(S0, tile(I.A, ld, t.i, t.k), ld);
         load_tile(S1, tile(I.A, ld, t.k, t.k), ld);
         __syncthreads();
-        tile_mm_lt(S0, S1, S2);                   // X_kk lower: its upper part is not read
+        mm_lt(S0, S1, S2);                        // X_kk lower: its upper part is not read
         __syncthreads();
         store_tile(Lt(t.i, t.k), T, S2, false);
         __syncthreads();
@@ -537,7 +690,7 @@ __global__ void __launch_bounds__(kDagThreads) potrf_dag_kernel(DagArgs g) {
         for (int e = threadIdx.x; e < T * T; e += kDagThreads)
           if (e % T < e / T) S0[e % T][e / T] = 0.0;
         __syncthreads();
-        tile_mm(S0, S1, false, S2, 1.0, false);
+        mm(S0, S1, false, S2, 1.0, false);
         __syncthreads();
         store_tile(tile(I.A, ld, t.i, t.j), ld, S2, false);
         __syncthreads();
@@ -549,7 +702,7 @@ __global__ void __launch_bounds__(kDagThreads) potrf_dag_kernel(DagArgs g) {
         load_tile(S1, Lt(t.j, t.k), T);
         load_tile(S2, tile(I.A, ld, t.i, t.j), ld);
         __syncthreads();
-        tile_mm(S0, S1, true, S2, -1.0, true);
+        mm(S0, S1, true, S2, -1.0, true);
         __syncthreads();
         store_tile(tile(I.A, ld, t.i, t.j), ld, S2, t.i == t.j);
         __syncthreads();
@@ -566,7 +719,7 @@ __global__ void __launch_bounds__(kDagThreads) potrf_dag_kernel(DagArgs g) {
           for (int e = threadIdx.x; e < T * T; e += kDagThreads)
             if (e % T < e / T) S1[e % T][e / T] = 0.0;
         __syncthreads();
-        tile_mm(S0, S1, false, S2, -1.0, !first);
+        mm(S0, S1, false, S2, -1.0, !first);
         __syncthreads();
         store_tile(tile(I.A, ld, t.i, t.j), ld, S2, false);
         __syncthreads();
@@ -640,7 +793,7 @@ size_t potrf_dag_state_ints(int p) { return (size_t)4 * p * p + p + 64 + 256; }
 // counters; n*n doubles are enough.
 bta_status potrf_dag_batch(int count, double* const* A, int n, int ld, double* const* scratch,
                            double* const* logdet_parts, int32_t* const* fail,
-                           const int32_t* fail_code, cudaStream_t s, int max_ctas) {
+                           const int32_t* fail_code, cudaStream_t s, int max_ctas, int tc) {
   const int p = n / T;
   if (n <= 0 || n % T || p > kMaxP || count < 1) return BTA_ERR_ARG;
   const size_t lt_doubles = (size_t)p * (p - 1) / 2 * T * T;
@@ -675,7 +828,18 @@ bta_status potrf_dag_batch(int count, double* const* A, int n, int ld, double* c
     int grid = std::min(g.total, sm_count() * dag_ctas_per_sm());
     const int cap = dag_max_ctas() > 0 ? dag_max_ctas() : max_ctas;
     if (cap > 0) grid = std::min(grid, std::max(2, cap));   // the chain and a bulk CTA
-    launch_prio(potrf_dag_kernel, dim3(grid), dim3(kDagThreads), s, g);
+    if (tc) {
+      static bool attr = false;   // the slices take the dynamic shared memory above 48 KB
+      if (!attr) {
+        BTA_CUDA_TRY(cudaFuncSetAttribute(potrf_dag_kernel<true>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          kOzTileSmem));
+        attr = true;
+      }
+      launch_prio_smem(potrf_dag_kernel<true>, dim3(grid), dim3(kDagThreads), kOzTileSmem, s, g);
+    } else {
+      launch_prio(potrf_dag_kernel<false>, dim3(grid), dim3(kDagThreads), s, g);
+    }
     BTA_LAUNCHED();
   }
   return BTA_OK;
