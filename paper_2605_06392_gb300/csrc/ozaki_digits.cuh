@@ -9,6 +9,17 @@
 namespace bta {
 namespace oz {
 
+// Conversions between FP32 and 32-bit integers of magnitude below 2^22 by
+// FP32 arithmetic against 1.5 2^23 (the FP32 adder's round to nearest even,
+// exact for integers): one add and one integer operation each, on the
+// full-rate pipes instead of the conversion unit.
+__device__ __forceinline__ int f2i_small(float x) {
+  return __float_as_int(x + 12582912.0f) - 0x4B400000;
+}
+__device__ __forceinline__ float i2f_small(int d) {
+  return __int_as_float(d + 0x4B400000) - 12582912.0f;
+}
+
 // X * 2^E rounded to the nearest double, from the integer X by integer
 // operations (the usual case); out-of-range exponents take ldexp.
 __device__ __forceinline__ double compose(long long X, int E) {
@@ -67,7 +78,7 @@ __device__ __forceinline__ void digits(double v, int er, float (&out)[S]) {
       } else {
         d = x;
       }
-      out[j] = (float)d * __int_as_float((127 - 7 * j) << 23);
+      out[j] = i2f_small(d) * __int_as_float((127 - 7 * j) << 23);
     }
   }
 }

@@ -38,6 +38,15 @@
 #include "common.cuh"
 #include "ozaki_digits.cuh"
 
+// Timeline hooks of the chain (compile-time empty in the library): a
+// measurement build that includes this file may define DAG_TRACE(event, step)
+// before the include to stamp the chain's phases of each diagonal step:
+// 0 the step's inputs are final (waits done), 1 the triangular product done,
+// 2 the symmetric update done, 3 the leaf done, 4 the step published.
+#ifndef DAG_TRACE
+#define DAG_TRACE(event, step) ((void)0)
+#endif
+
 namespace bta {
 namespace {
 
@@ -296,27 +305,34 @@ __device__ void tile_mm_oz(double (*X)[T + 1], double (*Y)[T + 1], bool ytrans, 
         ldsm_x2(yb + 2u * (uint32_t)(j * kOzPlane + br * kOzPitch + 16 * ks + bc), b[j][ks]);
       }
   }
-  long long tot[4] = {0, 0, 0, 0};
-  float low[4] = {0.f, 0.f, 0.f, 0.f};   // levels 6 and 7
+  // one accumulator per level, the pairs issued slice by slice of A so that
+  // consecutive MMAs go to different accumulators (no dependent chain)
+  float c[8][4];
 #pragma unroll
-  for (int L = 0; L < 8; ++L) {
-    float c[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int L = 0; L < 8; ++L)
 #pragma unroll
-    for (int i = 0; i <= L; ++i)
+    for (int q = 0; q < 4; ++q) c[L][q] = 0.f;
 #pragma unroll
-      for (int ks = 0; ks < 2; ++ks) mma_bf16(c, a[i][ks], b[L - i][ks]);
+  for (int ks = 0; ks < 2; ++ks)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (L < 6) tot[q] += __float2ll_rn(c[q] * 34359738368.0f);   // S_L 2^(35 - 7 L)
-      else low[q] += c[q];
-    }
-  }
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int j = 0; i + j < 8; ++j) mma_bf16(c[i + j], a[i][ks], b[j][ks]);
+  // S_L = c[L] 2^(7 L), |S_L| < 2^21: to integers by the exact FP32 rounding
+  // against 1.5 2^23 (no 64-bit conversions, which GB300 runs at its FP64
+  // rate); two levels 7 bits apart share one 32-bit integer, then
+  // tot = S_0 2^35 + S_1 2^28 + ... + S_5 + round(S_6 2^-7 + S_7 2^-14).
   const int g = lane >> 2, t = lane & 3;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    tot[q] += __float2ll_rn(low[q] * 34359738368.0f);
+    int sl[6];
+#pragma unroll
+    for (int L = 0; L < 6; ++L) sl[L] = oz::f2i_small(c[L][q] * __int_as_float((127 + 7 * L) << 23));
+    const int r67 = oz::f2i_small((c[6][q] + c[7][q]) * 34359738368.0f);
+    const long long tot = ((long long)(sl[0] * 128 + sl[1]) << 28) +
+                          ((long long)(sl[2] * 128 + sl[3]) << 14) + (sl[4] * 128 + sl[5]) + r67;
     const int r = 16 * mt + g + (q >> 1) * 8, c = 8 * nt + 2 * t + (q & 1);
-    const double v = oz::compose(tot[q], z.ex[r] + ey[c] - 2093);
+    const double v = oz::compose(tot, z.ex[r] + ey[c] - 2093);
     out[r][c] = accumulate ? fma(sign, v, out[r][c]) : sign * v;
   }
 }
@@ -597,6 +613,7 @@ __global__ void __launch_bounds__(kDagThreads) potrf_dag_kernel(DagArgs g) {
             return;
           }
         }
+        if (threadIdx.x == 0 && z == 0) DAG_TRACE(0, c);
         if (c > 0) {
           load_tile(S0, tile(I.A, ld, c, c - 1), ld);
           // W_cc into registers now, into S0 once the product has read it
@@ -612,6 +629,7 @@ __global__ void __launch_bounds__(kDagThreads) potrf_dag_kernel(DagArgs g) {
           __syncthreads();
           mm_lt(S0, S1, S2);                      // L_{c,c-1} = W X_{c-1,c-1}^T (S1)
           __syncthreads();
+          if (threadIdx.x == 0 && z == 0) DAG_TRACE(1, c);
 #pragma unroll
           for (int q = 0; q < T * T / kDagThreads; ++q) {
             const int e = threadIdx.x + kDagThreads * q;
@@ -623,17 +641,20 @@ __global__ void __launch_bounds__(kDagThreads) potrf_dag_kernel(DagArgs g) {
           if constexpr (TC) tile_mm_oz(S2, S2, true, false, S0, -1.0, true, ozs);   // W_cc -= L L^T
           else tile_syrk_lower(S2, S0);           // W_cc -= L L^T (lower)
           __syncthreads();
+          if (threadIdx.x == 0 && z == 0) DAG_TRACE(2, c);
         } else {
           load_tile(S0, tile(I.A, ld, 0, 0), ld);
           __syncthreads();
         }
         leaf(S0, S1, lcol, piv, rs);              // S1 = X_cc = L_cc^{-1}
+        if (threadIdx.x == 0 && z == 0) DAG_TRACE(3, c);
         store_tile(tile(I.A, ld, c, c), ld, S1, true);
         __syncthreads();
         if (threadIdx.x == 0) {
           __threadfence();
           st_release(&cntW[c * p + c], c);
           st_release(&doneF[c], 1);
+          if (z == 0) DAG_TRACE(4, c);
         }
         leaf_logdet(piv, &I.slots[c], I.fail, I.code);   // after the release: off the chain
         __syncthreads();
