@@ -550,6 +550,7 @@ struct OzqArgs {
   int group;                             // tile rows per group of the launch order
   int out_lower;
   int tri_a, tri_b;     // triangle of op(A) / op(B) (Tri): their zero K ranges are skipped
+  int reverse;          // take the tiles in reverse launch order (longest K ranges first)
   long long* partial;   // [splits][Np][Mp] integer sums, units 2^-35 of level 2
   int32_t* status;
 };
@@ -623,9 +624,10 @@ __global__ void __launch_bounds__(kQThreads, 1)
   // Tile order: groups of `group` tile rows, column by column inside a
   // group, so that the CTAs resident together share few A and B row blocks.
   const int mt_all = g.Mp / OM, nt_all = g.Np / QN;
-  const int grp = (int)blockIdx.x / (g.group * nt_all);
+  const int bx = g.reverse ? (int)gridDim.x - 1 - (int)blockIdx.x : (int)blockIdx.x;
+  const int grp = bx / (g.group * nt_all);
   const int gm = min(g.group, mt_all - grp * g.group);
-  const int in = (int)blockIdx.x - grp * g.group * nt_all;
+  const int in = bx - grp * g.group * nt_all;
   const int m0 = (grp * g.group + in % gm) * OM, n0 = (in / gm) * QN, z = blockIdx.z;
   if (g.out_lower && n0 > m0 + OM - 1) return;   // whole CTA exits before any set-up
   // this CTA's slabs of K: split z of `splits` near-equal ranges, taken in
@@ -936,7 +938,8 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kQThreads, 1)
   // Pair-tile order: groups of `group` pair rows, column by column inside a
   // group (as ozaki_gemm128_kernel, in units of 256 x 128 tiles).
   const uint32_t rank = cluster_rank();
-  const int pt = (int)blockIdx.x >> 1;
+  const int pt = g.reverse ? (int)(gridDim.x >> 1) - 1 - ((int)blockIdx.x >> 1)
+                           : (int)blockIdx.x >> 1;
   const int mt_all = g.Mp / kPM, nt_all = g.Np / QN;
   const int grp = pt / (g.group * nt_all);
   const int gm = min(g.group, mt_all - grp * g.group);
@@ -1605,6 +1608,11 @@ bta_status launch_ozaki(const Gemm& g, uint8_t* ws, int32_t* status, cudaStream_
     q.out_lower = g.out_lower;
     q.tri_a = g.triA;
     q.tri_b = g.triB;
+    // the K range of a tile grows with its row under a lower op(A) and with
+    // its column under an upper op(B), the ends of the launch order: start
+    // those first (the CTAs then finish closer together)
+    q.reverse = (g.triA == TRI_LOWER || g.triB == TRI_UPPER) &&
+                !(g.triA == TRI_UPPER || g.triB == TRI_LOWER);
     q.partial = partial;
     q.status = status;
     // a wave of pairs spans a near-square patch of 256 x 128 tiles
@@ -1630,6 +1638,11 @@ bta_status launch_ozaki(const Gemm& g, uint8_t* ws, int32_t* status, cudaStream_
     q.out_lower = g.out_lower;
     q.tri_a = g.triA;
     q.tri_b = g.triB;
+    // the K range of a tile grows with its row under a lower op(A) and with
+    // its column under an upper op(B), the ends of the launch order: start
+    // those first (the CTAs then finish closer together)
+    q.reverse = (g.triA == TRI_LOWER || g.triB == TRI_UPPER) &&
+                !(g.triA == TRI_UPPER || g.triB == TRI_LOWER);
     q.partial = partial;
     q.status = status;
     // ~sqrt(SMs) tile rows a group: a wave of CTAs spans a near-square patch
