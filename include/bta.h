@@ -116,16 +116,18 @@ typedef struct {
                           off-diagonal Schur products of both factorisations
                           and the selected-inversion products in split TF32
                           on the tensor cores (FP32 accumulation); diagonal
-                          block factorisation, log-determinants, arrow and tip
-                          in FP64 (diagonal blocks above 512 rows are split
-                          2 x 2, their inner products emulated to FP64
-                          accuracy as in mode 2); one FP64 refinement step on
+                          block factorisation to FP64 accuracy (FP64 pivots;
+                          blocks above 512 rows split 2 x 2, their inner
+                          products and the 32 x 32 tile products of the
+                          leaves emulated as in mode 2), log-determinants,
+                          arrow and tip in FP64; one FP64 refinement step on
                           x*.
                           2: emulated FP64 -- the same b x b products as in
-                          mode 1, and the inner products of split diagonal
-                          blocks, computed to FP64 accuracy on the BF16 tensor
-                          cores (8 slices, as bta_gemm_emulated; products with
-                          K > 5120 fall back to FP64); the arrow products and
+                          mode 1, with the arrow's rows and rank-a terms
+                          carried along, and the diagonal factor's inner and
+                          tile products, computed to FP64 accuracy on the
+                          BF16 tensor cores (8 slices, as bta_gemm_emulated;
+                          products with K > 5120 fall back to FP64);
                           everything else as in mode 0                        */
   int32_t use_graph;   /* 1: capture the evaluation in a CUDA graph, replay */
   int32_t streams;     /* thetas evaluated together for batch > 1 (1..16): their
@@ -171,10 +173,11 @@ bta_status bta_assemble(inla_model* m, const double* theta, int32_t which,
  * BTA_ERR_TIMEOUT: read fail_block.
  * precision: as inla_opts.precision.  0: FP64.  1: mixed -- the b x b
  * Schur-complement products (D_i -= L_B L_B^T, L_B = B L_D^{-T}) in split TF32
- * on the tensor cores, the diagonal factors, log-determinant, arrow and tip
- * in FP64 (relative error ~1e-9 in log|Q|, ~1e-6 in the factor; refine the
- * solve with bta_solve(refine = 1)).  2: emulated FP64 -- the same products
- * to FP64 accuracy on the BF16 tensor cores.  Modes 1 and 2 allocate their
+ * on the tensor cores, the diagonal factors (FP64 pivots, emulated-FP64 inner
+ * products), log-determinant, arrow and tip in FP64 (relative error ~1e-9 in
+ * log|Q|, ~1e-6 in the factor; refine the solve with bta_solve(refine = 1)).
+ * 2: emulated FP64 -- the same products, the arrow's carried along, to FP64
+ * accuracy on the BF16 tensor cores.  Modes 1 and 2 allocate their
  * operand copies with cudaMallocAsync on the stream, as the workspace of
  * every mode.  Sets state FACTORED.
  */
