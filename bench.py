@@ -166,6 +166,12 @@ class ClockSampler:
 # the FP64 CPU oracle (cpu_baseline and the reference arm)
 # ----------------------------------------------------------------------------
 FULL_NT = 192
+# DRAM bytes (read + write) of one launch of the emulated product kernel at
+# 4800 x 4800 x 4800, from an ncu capture of that launch (dram__bytes_read.sum
+# 2.649 GB + dram__bytes_write.sum 0.2015 GB; `--metrics ... -k
+# regex:ozaki_gemm128 -c 1` on `bench.py --mode gemm --precision 2 --gemm-n
+# 4800`).  The slices themselves are 0.75 GB: L2 absorbs most tile re-reads.
+GEMM4800_DRAM_BYTES = 2.851e9
 
 
 def oracle_cut_problem(nt):
@@ -644,7 +650,7 @@ def main():
                                                       f"{kb} x {kb} x {kb} (BF16 slices)",
                          "achieved": achieved, "peak": peaks["bf16_tflops_sustained"],
                          "unit": "TFLOP/s", "frac": achieved / peaks["bf16_tflops_sustained"],
-                         "traffic": None,
+                         "traffic": GEMM4800_DRAM_BYTES if kb == 4800 else None,
                          "launch_ms": kms,
                          "algorithmic": f"36 x 2 x {kb}^3 BF16 flop per launch",
                          "fp64_equivalent_tflops": 2.0 * float(kb) ** 3 / (kms * 1e-3) / 1e12,
