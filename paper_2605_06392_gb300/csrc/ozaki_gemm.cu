@@ -553,6 +553,24 @@ struct OzqArgs {
   int reverse;          // take the tiles in reverse launch order (longest K ranges first)
   long long* partial;   // [splits][Np][Mp] integer sums, units 2^-35 of level 2
   int32_t* status;
+  // Compose in the epilogue (one split, one-CTA kernel): each drain thread
+  // turns its row's integer sums into C itself, as ozaki_compose_kernel would
+  // (same operations, same bits), instead of writing them to `partial`.
+  int fuse;
+  int M, N;             // rows / columns of C (the padding is not written)
+  int amode, bmode;
+  double alpha, beta;
+  double* C;
+  int ldc;
+  const double* Cin;
+  int ldcin;
+  int c_rows;           // rows m >= c_rows go to C2 / Cin2 (INT_MAX: none)
+  double* C2;
+  int ldc2;
+  const double* Cin2;
+  int ldcin2;
+  const int* exA;
+  const int* exB;
 };
 
 // The 32-wide K slabs [kb, ke) of a tile with output rows m0 .. m0 + rows - 1
@@ -823,7 +841,26 @@ __global__ void __launch_bounds__(kQThreads, 1)
         mbar_arrive(smem_u32(&bars[kAccEmpty]));
       }
     }
-    if (!failed) {
+    if (!failed && g.fuse) {
+      // a warp's lanes are 32 consecutive rows: each column's stores coalesce
+      const int m = m0 + row;
+      if (m < g.M) {
+        const bool top = m < g.c_rows;
+        double* const Cm = top ? g.C + m : g.C2 + (m - g.c_rows);
+        const double* const Cinm = top ? g.Cin + m : g.Cin2 + (m - g.c_rows);
+        const int ldc = top ? g.ldc : g.ldc2, ldcin = top ? g.ldcin : g.ldcin2;
+        const bool lower = g.out_lower && top;
+        const int ea = g.exA[m] - 2093;
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+          const int n = n0 + col0 + q;
+          if (n >= g.N || (lower && m < n)) continue;
+          double out = compose(acc[q], ea + g.exB[n]);
+          out = scale_add(out, g.amode, g.alpha, g.bmode, g.beta, Cinm + (int64_t)n * ldcin);
+          Cm[(int64_t)n * ldc] = out;
+        }
+      }
+    } else if (!failed) {
       long long* part = g.partial + (int64_t)z * g.Mp * g.Np + (m0 + row) +
                         (int64_t)(n0 + col0) * g.Mp;
 #pragma unroll
@@ -1601,7 +1638,7 @@ bta_status launch_ozaki(const Gemm& g, uint8_t* ws, int32_t* status, cudaStream_
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kPSmem));
       attrp = true;
     }
-    OzqArgs q;
+    OzqArgs q{};
     q.Mp = L.Mp; q.Np = L.Np; q.Bp = bpitch;
     q.nk = L.Kp / OK16;
     q.splits = plan.splits;
@@ -1631,7 +1668,7 @@ bta_status launch_ozaki(const Gemm& g, uint8_t* ws, int32_t* status, cudaStream_
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, kQSmem));
       attr128 = true;
     }
-    OzqArgs q;
+    OzqArgs q{};
     q.Mp = L.Mp; q.Np = L.Np; q.Bp = bpitch;
     q.nk = L.Kp / OK16;
     q.splits = plan.splits;
@@ -1647,12 +1684,26 @@ bta_status launch_ozaki(const Gemm& g, uint8_t* ws, int32_t* status, cudaStream_
     q.status = status;
     // ~sqrt(SMs) tile rows a group: a wave of CTAs spans a near-square patch
     q.group = std::min(L.Mp / OM, std::max(1, (int)std::lround(std::sqrt((double)sm_count()))));
+    q.fuse = 0;
+    if (!plan.pair && plan.splits == 1) {   // C composed in the kernel's epilogue
+      q.fuse = 1;
+      q.M = M; q.N = N;
+      q.amode = alpha_mode(g.alpha); q.bmode = beta_mode(g.beta);
+      q.alpha = g.alpha; q.beta = g.beta;
+      q.C = g.C; q.ldc = g.ldc;
+      q.Cin = g.Cin ? g.Cin : g.C; q.ldcin = g.Cin ? g.ldcin : g.ldc;
+      q.c_rows = g.C2 ? g.c_rows : INT_MAX;
+      q.C2 = g.C2; q.ldc2 = g.ldc2;
+      q.Cin2 = g.Cin2 ? g.Cin2 : g.C2; q.ldcin2 = g.Cin2 ? g.ldcin2 : g.ldc2;
+      q.exA = exA; q.exB = same ? exA : exB;
+    }
     if (!plan.pair) {
       if (marks) BTA_CUDA_TRY(cudaEventRecord(marks[0], s));
       ozaki_gemm128_kernel<<<dim3((L.Mp / OM) * (L.Np / QN), 1, plan.splits), kQThreads,
                              kQSmem, s>>>(mA, mB, q);
       BTA_LAUNCHED();
       if (marks) BTA_CUDA_TRY(cudaEventRecord(marks[1], s));
+      if (q.fuse) return BTA_OK;
     }
     ComposeArgs c;
     c.M = M; c.N = N; c.Mp = L.Mp; c.Np = L.Np; c.splits = plan.splits;
