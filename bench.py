@@ -167,11 +167,12 @@ class ClockSampler:
 # ----------------------------------------------------------------------------
 FULL_NT = 192
 # DRAM bytes (read + write) of one launch of the emulated product kernel at
-# 4800 x 4800 x 4800, from an ncu capture of that launch (dram__bytes_read.sum
-# 2.649 GB + dram__bytes_write.sum 0.2015 GB; `--metrics ... -k
-# regex:ozaki_gemm128 -c 1` on `bench.py --mode gemm --precision 2 --gemm-n
-# 4800`).  The slices themselves are 0.75 GB: L2 absorbs most tile re-reads.
-GEMM4800_DRAM_BYTES = 2.851e9
+# 4800 x 4800 x 4800 (composing C in its epilogue), from an ncu capture of that
+# launch (dram__bytes_read.sum 2.651 GB + dram__bytes_write.sum 0.201 GB;
+# `--metrics ... -k regex:ozaki_gemm128 -c 1` on `bench.py --mode gemm
+# --precision 2 --gemm-n 4800`).  The slices themselves are 0.75 GB: L2 absorbs
+# most tile re-reads.
+GEMM4800_DRAM_BYTES = 2.852e9
 
 
 def oracle_cut_problem(nt):
