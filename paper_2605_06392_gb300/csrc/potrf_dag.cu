@@ -1,5 +1,8 @@
 // Diagonal-block Cholesky factor and inverse as one persistent kernel over a
-// tile task graph (FP64, 32 x 32 tiles, p = n / 32 tile rows).
+// tile task graph (FP64 results, 32 x 32 tiles, p = n / 32 tile rows).  Its
+// tile products run as FP64 FMAs, or (the tensor-core modes, kernel
+// instance TC) emulated in FP64 from BF16 slices on warp-level tensor-core
+// MMAs (tile_mm_oz); pivots, reciprocals and log-dets stay in FP64.
 //
 // Same contract as the recursive potrf_inv: on return the lower triangle of
 // A holds L^{-1} (A = L L^T), one log-det slot per diagonal tile, the failure
